@@ -1,0 +1,343 @@
+"""Benchmark: EOFA Dirac-equation solve to true residual 1e-10 on one GB300.
+
+A step is one complete EOFA solve (H form, Eq. generic_eofa_system) of the
+16^3x32, Ls=16 Moebius workload (b=1.5, c=0.5, M5=1.8, m1=0.04, m2=1.0,
+m3=0.04, shift chirality +, beta=-1, antiperiodic time, random SU(3) links
+exp(i 0.5 H)) with mixed-precision defect correction: FP32 inner CGNR on the
+even-odd Cayley-form Schur complement, FP64 outer residual and update.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--inner f32|f16|bf16|f64]
+    python bench.py --impl reference ...     # the FP64 CPU oracle, bounded sample
+
+Prints one JSON line (rank 0).  value = seconds per solve over the whole job
+(max over ranks of the timed region / solves done by all ranks); with N > 1
+every rank solves its own right-hand side on its own GPU (replicas, weak
+scaling).  Inputs are resident in HBM before the timed region; the solver's
+working set (~1.2 GB of FP32/FP64 fields) is far larger than L2, so no flush
+is needed.  e2e repeats the solve through the public API with the
+right-hand side copied from pinned host memory and the solution copied back
+inside the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "EOFA solve sec to r=1e-10 & dslash HBM GB/s: mixed/learned vs plain FP64 CG"
+WORKLOAD = dict(name="16^3x32_Ls16", dims=(16, 16, 16, 32), Ls=16, eps=0.5, gauge_seed=1, rhs_seed=1001,
+                action=dict(M5=1.8, b=1.5, c=0.5, m1=0.04, m2=1.0, m3=0.04, beta=-1.0, pm=1, t_bc=-1))
+TOL = 1e-10
+KERNEL_SOURCES = ["paper_1706_05843_gb300/csrc/dslash.cuh", "paper_1706_05843_gb300/csrc/common.cuh"]
+
+
+def workload_desc(inner):
+    w = WORKLOAD
+    a = w["action"]
+    return (f"EOFA H-form solve {'x'.join(map(str, w['dims']))} Ls={w['Ls']} Moebius b={a['b']} c={a['c']} "
+            f"M5={a['M5']} m1={a['m1']} m2={a['m2']} m3={a['m3']} shift + beta={a['beta']}, random SU(3) "
+            f"eps={w['eps']}, eo Cayley-form CGNR, {inner} inner / FP64 defect correction to r=1e-10")
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.proc = None
+        self.buf = None
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.out = open(os.devnull, "w")
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r for r in csv.reader(io.StringIO(out)) if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def ncu_traffic():
+    """DRAM bytes per hop launch from the committed ncu summary, if it was
+    taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "hop_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    return d
+
+
+def oracle_sample(iters_per_sample, samples=1):
+    """Time the FP64 CPU oracle's CGNR on the full workload (bounded sample)
+    and scale to seconds per solve with the oracle's recorded iteration count."""
+    import oracle
+    from paper_1706_05843_gb300 import inputs as I
+    oracle.build()
+    w = WORKLOAD
+    U = I.gauge_field(w["dims"], w["eps"], w["gauge_seed"])
+    phi = I.gaussian_fermion(w["dims"], w["Ls"], w["rhs_seed"])
+    o = oracle.Oracle(oracle.Action(dims=w["dims"], Ls=w["Ls"], **w["action"]), U)
+    counts = os.path.join(ROOT, "oracle", "iteration_counts.json")
+    n_iter = None
+    if os.path.exists(counts):
+        n_iter = json.load(open(counts)).get(w["name"], {}).get("iters")
+    times = []
+    for _ in range(samples):
+        t0 = time.perf_counter()
+        _, st = o.solve_h(phi, tol=1e-300, maxit=iters_per_sample)
+        times.append((time.perf_counter() - t0) / max(st.iters, 1))
+    per_iter = statistics.median(times)
+    return per_iter, n_iter, oracle.num_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    per = []
+    for i in range(warm + steps):
+        pi, n_iter, cores = oracle_sample(args.ref_iters)
+        if i >= warm:
+            per.append(pi)
+    per_iter = statistics.median(per)
+    if n_iter is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle iteration count not recorded"}))
+        return
+    val = per_iter * n_iter
+    sample = (f"{args.ref_iters} oracle CGNR iterations per step on the full workload, "
+              f"scaled by the oracle's recorded {n_iter} iterations to r=1e-10")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "s/solve", "n_gpus": ws,
+        "steps": steps, "warmup": warm, "ms_per_step": per_iter * args.ref_iters * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_desc("FP64 oracle (unpreconditioned)")},
+        "cpu_baseline": {"value": val, "unit": "s/solve", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "s/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_1706_05843_gb300 import binding as B
+    from paper_1706_05843_gb300 import build as BLD
+    from paper_1706_05843_gb300 import inputs as I
+    if not os.path.exists(B.LIB_PATH):
+        BLD.build()
+    B.lib()
+
+    w = WORKLOAD
+    U = I.gauge_field(w["dims"], w["eps"], w["gauge_seed"])
+    phi = I.gaussian_fermion(w["dims"], w["Ls"], w["rhs_seed"] + rank)
+    solver = B.Solver(U, w["dims"], w["Ls"], **w["action"])
+    rhs = torch.from_numpy(phi).to(dev)
+    sol = torch.empty_like(rhs)
+    stream = torch.cuda.current_stream()
+    opts = dict(tol=TOL, inner=args.inner)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        solver.solve(rhs, out=sol, **opts)
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    time.sleep(0.3)
+    stats = []
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, st = solver.solve(rhs, out=sol, kernel_timing=True, **opts)
+        stats.append(st.as_dict())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    elapsed = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    clocks = sampler.stop() if sampler else None
+    value = elapsed / (args.steps * ws)
+    ms_per_step = elapsed / args.steps * 1e3
+    hop_ms = sum(s["hop_ms"] for s in stats)
+    hop_bytes = sum(s["hop_bytes"] for s in stats)
+    hop_n = sum(s["hop_launches"] for s in stats)
+    launches = int(statistics.median([s["kernel_launches"] for s in stats]))
+
+    # end to end through the public API: pinned host rhs -> device, solve, -> host
+    host_rhs = torch.from_numpy(phi).pin_memory()
+    host_sol = torch.empty_like(host_rhs).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        d_rhs = host_rhs.to(dev, non_blocking=True)
+        out, _ = solver.solve(d_rhs, **opts)
+        host_sol.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_val = max_over_ranks(e0.elapsed_time(e1) / 1e3) / (e2e_steps * ws)
+
+    # the other precisions once each, outside the timed region
+    extra = {}
+    if rank == 0 and not args.quick:
+        for inner in ["f64", "f32", "f16", "bf16"]:
+            if inner == args.inner:
+                continue
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = solver.solve(rhs, out=sol, tol=TOL, inner=inner, kernel_timing=True, check=False)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            extra[inner] = {"s_per_solve": dt, "true_res": st.true_res, "outer": st.outer_iters,
+                            "inner_iters": st.inner_iters, "status": st.status,
+                            "hop_GBps": st.hop_bytes / (st.hop_ms * 1e-3) / 1e9 if st.hop_ms else None}
+
+    if rank != 0:
+        return
+    main = stats[-1]
+    peak, peak_kind = peaks()
+    achieved = hop_bytes / (hop_ms * 1e-3) / 1e9 if hop_ms > 0 else None
+    tr = ncu_traffic()
+    traffic = None
+    if tr is not None:
+        traffic = tr.get(f"{args.inner}_bytes_per_launch")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "kernel": f"hop_kernel<{args.inner}, Ls=16> (4 kinds: Schur and Schur^dag halves)",
+                "bytes_per_launch": hop_bytes / hop_n if hop_n else None,
+                "launch_ms": hop_ms / hop_n if hop_n else None, "launches_timed": hop_n,
+                "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        pi, n_iter, cores = oracle_sample(args.ref_iters)
+        if n_iter:
+            cpu = {"value": pi * n_iter, "unit": "s/solve", "cores": cores, "kind": "oracle",
+                   "sample": f"{args.ref_iters} FP64 oracle CGNR iterations (unpreconditioned) on the full "
+                             f"workload, {pi:.3f} s/iteration, scaled by the oracle's recorded {n_iter} "
+                             f"iterations to r=1e-10"}
+    f64 = extra.get("f64", {}).get("s_per_solve")
+    line = {
+        "metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.inner != "f64" else "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(args.inner), "lattice": "16x16x16x32", "Ls": 16,
+                   "inner": args.inner, "tol": TOL, "parallelism": f"replicas{ws}",
+                   "l2": "working set > L2 (about 1.2 GB of fields); no flush"},
+        "e2e": {"value": e2e_val, "unit": "s/solve", "h2d_bytes_per_step": int(host_rhs.numel() * 16),
+                "d2h_bytes_per_step": int(host_sol.numel() * 16)},
+        "gpu_launches": launches * args.steps,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "solve": {"true_res": main["true_res"], "outer_iters": main["outer_iters"],
+                  "inner_iters": main["inner_iters"], "kernel_launches_per_solve": launches},
+        "other_precisions": extra,
+        "speedup_vs_fp64": (f64 / value) if f64 and ws == 1 else None,
+    }
+    print(json.dumps(line))
+    solver.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--inner", default="f32", choices=["f64", "f32", "f16", "bf16"])
+    ap.add_argument("--ref-iters", type=int, default=8, help="oracle iterations per CPU sample")
+    ap.add_argument("--quick", action="store_true", help="skip the other-precision solves")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * eofa.h -- C ABI of the GB300 EOFA Dirac-equation solver (libeofa.so).
+ *
+ * The library solves the exact one flavor algorithm (EOFA) Dirac equation of
+ * Jung, Kelly, Mawhinney, Murphy, arXiv:1706.05843,
+ *
+ *     ( H(m1) + beta Delta_pm(m2, m3) P_pm ) psi = phi,            Eq. (generic_eofa_system)
+ *     H(m) = gamma_5 R_5 D_EOFA(m),                                 Sec. II
+ *
+ * for Moebius domain wall fermions.  Internally it rotates by gamma_5 R_5
+ * (Eq. non_hermit_sys), right-preconditions with D~(m1)^-1 (Cayley form,
+ * Eq. precond_mobius_eofa_system), so that the operator actually inverted is
+ *
+ *     K = D_DWF(m1) + pm * beta * u_pm (x) v_pm P_pm,               App. B
+ *     D_DWF(m) = (b D_W + 1) + (c D_W - 1) L(m),                    Eq. (Ddwf)
+ *
+ * and solves the 4D even-odd Schur complement K_oo - K_oe K_ee^-1 K_eo
+ * (App. B) by conjugate gradient on the normal equations, with the site-
+ * diagonal inverse applied through the Sherman-Morrison formula
+ * (Eq. sherman_morrison_mobius_inv).  psi = D~(m1) psi' recovers the
+ * H-form solution.
+ *
+ * Notation: b, c are the Moebius coefficients b5, c5 of Eq. (Ddwf); the
+ * paper writes them as b5 = c + d, c5 = c - d with d = 1/2.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Lattice dims[4] = {X, Y, Z, T}; every extent even (checkerboarding),
+ *    Ls even and in {4, 8, 12, 16} (EOFA_ERR_UNSUPPORTED otherwise).
+ *  - Gauge field: device memory, complex128 (interleaved re, im doubles),
+ *    C order U[t][z][y][x][mu][row][col], mu = 0..3 = x, y, z, t.  Links
+ *    must be special unitary to 1e-10: the library keeps two rows and
+ *    rebuilds the third as conj(row0 x row1).
+ *  - 5D fermion fields: device memory, complex128,
+ *    psi[t][z][y][x][s][spin][colour], 24 * Ls * X*Y*Z*T doubles.
+ *  - Gamma matrices in the chiral basis: gamma_k = [[0,-i sigma_k],[i sigma_k,0]],
+ *    gamma_4 = [[0,1],[1,0]], gamma_5 = diag(1,1,-1,-1); P_pm = (1 pm gamma_5)/2.
+ *  - Hops across the t boundary carry t_bc (-1: antiperiodic); space is
+ *    periodic.
+ *  - Ownership: all field pointers belong to the caller and are not kept
+ *    after a call returns.  eofa_create copies the gauge field into the
+ *    context (compressed, even-odd blocked); the context owns its device
+ *    workspace until eofa_destroy.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *    eofa_apply* enqueue their work and return without synchronising;
+ *    eofa_solve* return after the solve has finished (the caller's stream
+ *    is ordered before and after it).  One context must not be used by
+ *    two calls at the same time.
+ *  - Errors: every call returns an eofa_status and never aborts or exits.
+ *    eofa_last_error(ctx) gives a message for the last failing call.
+ *    Non-convergence still writes the best solution and its statistics.
+ */
+#ifndef EOFA_H
+#define EOFA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EOFA_OK = 0,
+    EOFA_ERR_ARG = 1,           /* bad argument (NULL, odd extent, |pm| != 1, non-SU(3) links) */
+    EOFA_ERR_UNSUPPORTED = 2,   /* Ls outside the compiled set, |gamma/alpha| >= 1, ... */
+    EOFA_ERR_SINGULAR = 3,      /* N(m) = 0 or Sherman-Morrison denominator ~ 0 */
+    EOFA_ERR_NOT_CONVERGED = 4, /* max_iter / max_outer reached */
+    EOFA_ERR_NONFINITE = 5,     /* NaN or Inf met in a reduction */
+    EOFA_ERR_TIMEOUT = 6,       /* timeout_ms exceeded */
+    EOFA_ERR_CUDA = 7,          /* a CUDA runtime call failed */
+    EOFA_ERR_OOM = 8            /* device allocation failed */
+} eofa_status;
+
+/* Storage precision of the inner Krylov solver (arithmetic is FP64 for
+ * EOFA_F64 and FP32 for the others). */
+typedef enum {
+    EOFA_F64 = 0,
+    EOFA_F32 = 1,
+    EOFA_F16 = 2,   /* half spinors with one FP32 scale per 5D site */
+    EOFA_BF16 = 3
+} eofa_prec;
+
+/* Physics parameters (Eq. Ddwf, Eq. generic_eofa_system). */
+typedef struct {
+    int dims[4];      /* X, Y, Z, T (each even) */
+    int Ls;           /* fifth-dimension extent (even) */
+    double M5;        /* domain wall height */
+    double b, c;      /* Moebius b5, c5 */
+    double m1;        /* mass of H(m1), of D_DWF(m1) and of D~(m1) */
+    double m2, m3;    /* masses of the shift Delta_pm(m2, m3) */
+    double beta;      /* coefficient of the shift (0: plain D_DWF / H solve) */
+    int pm;           /* +1 or -1: chirality of the shift term */
+    int t_bc;         /* +1 periodic or -1 antiperiodic time */
+} eofa_params;
+
+/* Solver options.  Zero-initialise and set what you need; tol is required. */
+typedef struct {
+    double tol;          /* target true relative residual ||b - A x|| / ||b|| */
+    int max_iter;        /* cap on total inner CG iterations (0: 100000) */
+    int inner;           /* eofa_prec of the inner solver (EOFA_F64 = plain FP64 CG) */
+    double inner_tol;    /* inner relative tolerance of defect correction (0: per precision) */
+    int max_outer;       /* cap on outer defect-correction steps (0: 100) */
+    int precond;         /* 0: none.  1: learned preconditioner (needs eofa_set_preconditioner) */
+    int use_guess;       /* 1: sol holds an initial guess on entry */
+    int rhs_form;        /* 0: H form, rhs = phi, sol = psi.  1: K form, rhs = b, sol = psi' (K psi' = b) */
+    int kernel_timing;   /* 1: time every hop kernel with CUDA events (no graph capture) */
+    int pad_;
+    long timeout_ms;     /* 0: none; otherwise wall-clock limit checked between chunks */
+} eofa_solve_opts;
+
+/* Statistics of one solve. */
+typedef struct {
+    int status;          /* eofa_status of the solve */
+    int outer_iters;     /* defect-correction steps (1 for a plain FP64 solve) */
+    int inner_iters;     /* CG iterations summed over all inner solves */
+    int hop_launches;    /* hop kernels timed (kernel_timing = 1), else 0 */
+    double true_res;     /* FP64 ||rhs - A sol|| / ||rhs|| on the full lattice */
+    double recur_res;    /* last recursively updated residual (relative) */
+    double seconds;      /* wall-clock time of the call */
+    double hop_ms;       /* summed hop-kernel time (kernel_timing = 1) */
+    double hop_bytes;    /* algorithmic bytes moved by the timed hop kernels */
+    long kernel_launches;/* kernels this library launched during the call */
+} eofa_solve_stats;
+
+typedef struct eofa_ctx eofa_ctx;
+
+/* Create a context: validates params, builds the fifth-dimension
+ * coefficients (u_pm, v_pm, the cyclic-bidiagonal inverse and the
+ * Sherman-Morrison factors of App. B) and copies the gauge field.
+ * gauge: device pointer, layout above.  *out is NULL on failure. */
+eofa_status eofa_create(const eofa_params *p, const void *gauge, void *stream,
+                        eofa_ctx **out);
+
+/* out = K in, K = D_DWF(m1) + pm beta u_pm (x) v_pm P_pm (App. B).
+ * in, out: device complex128 5D fields; in != out. */
+eofa_status eofa_apply(eofa_ctx *ctx, const void *in, void *out, void *stream);
+
+/* out = K^dag in. */
+eofa_status eofa_apply_dag(eofa_ctx *ctx, const void *in, void *out, void *stream);
+
+/* out = (H(m1) + beta Delta_pm(m2,m3) P_pm) in = g5 R5 K D~(m1)^-1 in
+ * (Eq. generic_eofa_system). */
+eofa_status eofa_apply_h(eofa_ctx *ctx, const void *in, void *out, void *stream);
+
+/* Solve the EOFA system.  rhs, sol: device complex128 5D fields.
+ * rhs_form 0 (H form): (H(m1) + beta Delta_pm P_pm) sol = rhs.
+ * rhs_form 1 (K form): K sol = rhs.
+ * Plain FP64 CGNR when opts->inner == EOFA_F64, otherwise restarted
+ * defect correction (FP64 outer residual and update, inner CGNR in the
+ * requested storage precision), Sec. V.A.  stats may be NULL. */
+eofa_status eofa_solve(eofa_ctx *ctx, const void *rhs, void *sol,
+                       const eofa_solve_opts *opts, eofa_solve_stats *stats,
+                       void *stream);
+
+/* out[i] = K in[i] (dag = 0) or K^dag in[i] (dag = 1) for n contexts,
+ * which may have different lattices. */
+eofa_status eofa_apply_batched(eofa_ctx *const *ctx, int n, const void *const *in,
+                               void *const *out, int dag, void *stream);
+
+/* n independent solves (one per context and rhs), possibly of different
+ * lattice sizes; stats is an array of n entries (or NULL).  Returns the
+ * first non-OK status. */
+eofa_status eofa_solve_batched(eofa_ctx *const *ctx, int n, const void *const *rhs,
+                               void *const *sol, const eofa_solve_opts *opts,
+                               eofa_solve_stats *stats, void *stream);
+
+/* Release the context and all its device memory. */
+void eofa_destroy(eofa_ctx *ctx);
+
+/* Static description of a status code. */
+const char *eofa_status_string(eofa_status s);
+
+/* Message of the last failing call on ctx (empty string if none). */
+const char *eofa_last_error(const eofa_ctx *ctx);
+
+/* Algorithmic bytes of one hop-kernel launch in storage precision prec:
+ * per output 5D site 2*24 reals of spinor plus 8 two-row links shared
+ * over Ls, plus 24 reals of the local vector when the kernel reads one. */
+double eofa_hop_bytes(const eofa_ctx *ctx, int prec, int with_local);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EOFA_H */

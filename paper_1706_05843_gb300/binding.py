@@ -1,0 +1,243 @@
+"""ctypes binding of libeofa.so (include/eofa.h): argument marshalling only.
+
+Every step of the solve runs inside the CUDA library.  Device memory and
+streams come from PyTorch (complex128 CUDA tensors, torch streams).  If the
+library is missing this module raises: there is no CPU fallback.
+
+The functions keep the C names (``eofa_create``, ``eofa_apply``, ...); the
+``Solver`` class is a small convenience wrapper over them.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libeofa.so")
+
+F64, F32, F16, BF16 = 0, 1, 2, 3
+PREC = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+
+STATUS = {0: "EOFA_OK", 1: "EOFA_ERR_ARG", 2: "EOFA_ERR_UNSUPPORTED", 3: "EOFA_ERR_SINGULAR",
+          4: "EOFA_ERR_NOT_CONVERGED", 5: "EOFA_ERR_NONFINITE", 6: "EOFA_ERR_TIMEOUT",
+          7: "EOFA_ERR_CUDA", 8: "EOFA_ERR_OOM"}
+
+
+class EofaError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+
+
+class eofa_params(C.Structure):
+    _fields_ = [("dims", C.c_int * 4), ("Ls", C.c_int), ("M5", C.c_double), ("b", C.c_double),
+                ("c", C.c_double), ("m1", C.c_double), ("m2", C.c_double), ("m3", C.c_double),
+                ("beta", C.c_double), ("pm", C.c_int), ("t_bc", C.c_int)]
+
+
+class eofa_solve_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("inner", C.c_int),
+                ("inner_tol", C.c_double), ("max_outer", C.c_int), ("precond", C.c_int),
+                ("use_guess", C.c_int), ("rhs_form", C.c_int), ("kernel_timing", C.c_int),
+                ("pad_", C.c_int), ("timeout_ms", C.c_long)]
+
+
+class eofa_solve_stats(C.Structure):
+    _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("inner_iters", C.c_int),
+                ("hop_launches", C.c_int), ("true_res", C.c_double), ("recur_res", C.c_double),
+                ("seconds", C.c_double), ("hop_ms", C.c_double), ("hop_bytes", C.c_double),
+                ("kernel_launches", C.c_long)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# name -> (argtypes, restype); must match include/eofa.h
+_vp = C.c_void_p
+SIGNATURES = {
+    "eofa_create": ([C.POINTER(eofa_params), _vp, _vp, C.POINTER(_vp)], C.c_int),
+    "eofa_apply": ([_vp, _vp, _vp, _vp], C.c_int),
+    "eofa_apply_dag": ([_vp, _vp, _vp, _vp], C.c_int),
+    "eofa_apply_h": ([_vp, _vp, _vp, _vp], C.c_int),
+    "eofa_solve": ([_vp, _vp, _vp, C.POINTER(eofa_solve_opts), C.POINTER(eofa_solve_stats), _vp], C.c_int),
+    "eofa_apply_batched": ([C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp), C.c_int, _vp], C.c_int),
+    "eofa_solve_batched": ([C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp),
+                            C.POINTER(eofa_solve_opts), C.POINTER(eofa_solve_stats), _vp], C.c_int),
+    "eofa_destroy": ([_vp], None),
+    "eofa_status_string": ([C.c_int], C.c_char_p),
+    "eofa_last_error": ([_vp], C.c_char_p),
+    "eofa_hop_bytes": ([_vp, C.c_int, C.c_int], C.c_double),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libeofa.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1706_05843_gb300.build.build() first")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _dptr(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()):
+        raise TypeError("fields must be contiguous complex128 CUDA tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _check(ctx, status):
+    if status != 0:
+        msg = lib().eofa_last_error(ctx).decode() if ctx else ""
+        raise EofaError(status, msg)
+
+
+def make_params(dims, Ls, M5=1.8, b=1.5, c=0.5, m1=0.04, m2=1.0, m3=0.04, beta=-1.0, pm=1, t_bc=-1):
+    p = eofa_params()
+    for i in range(4):
+        p.dims[i] = int(dims[i])
+    p.Ls, p.M5, p.b, p.c = int(Ls), float(M5), float(b), float(c)
+    p.m1, p.m2, p.m3, p.beta = float(m1), float(m2), float(m3), float(beta)
+    p.pm, p.t_bc = int(pm), int(t_bc)
+    return p
+
+
+def make_opts(tol=1e-10, inner="f64", inner_tol=0.0, max_iter=0, max_outer=0, use_guess=False,
+              rhs_form=0, kernel_timing=False, timeout_ms=0, precond=0):
+    o = eofa_solve_opts()
+    o.tol, o.inner, o.inner_tol = float(tol), PREC[inner] if isinstance(inner, str) else int(inner), float(inner_tol)
+    o.max_iter, o.max_outer, o.precond = int(max_iter), int(max_outer), int(precond)
+    o.use_guess, o.rhs_form, o.kernel_timing = int(use_guess), int(rhs_form), int(kernel_timing)
+    o.timeout_ms = int(timeout_ms)
+    return o
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers
+# ---------------------------------------------------------------------------
+def eofa_create(params, gauge, stream=None):
+    ctx = C.c_void_p()
+    _check(None, lib().eofa_create(C.byref(params), _dptr(gauge), _stream(stream), C.byref(ctx)))
+    return ctx
+
+
+def eofa_apply(ctx, inp, out, stream=None):
+    _check(ctx, lib().eofa_apply(ctx, _dptr(inp), _dptr(out), _stream(stream)))
+
+
+def eofa_apply_dag(ctx, inp, out, stream=None):
+    _check(ctx, lib().eofa_apply_dag(ctx, _dptr(inp), _dptr(out), _stream(stream)))
+
+
+def eofa_apply_h(ctx, inp, out, stream=None):
+    _check(ctx, lib().eofa_apply_h(ctx, _dptr(inp), _dptr(out), _stream(stream)))
+
+
+def eofa_solve(ctx, rhs, sol, opts, stream=None, check=True):
+    st = eofa_solve_stats()
+    s = lib().eofa_solve(ctx, _dptr(rhs), _dptr(sol), C.byref(opts), C.byref(st), _stream(stream))
+    if check:
+        _check(ctx, s)
+    return st
+
+
+def eofa_apply_batched(ctxs, ins, outs, dag=False, stream=None):
+    n = len(ctxs)
+    ca = (C.c_void_p * n)(*[c.value for c in ctxs])
+    ia = (C.c_void_p * n)(*[_dptr(t).value for t in ins])
+    oa = (C.c_void_p * n)(*[_dptr(t).value for t in outs])
+    _check(None, lib().eofa_apply_batched(ca, n, ia, oa, int(dag), _stream(stream)))
+
+
+def eofa_solve_batched(ctxs, rhss, sols, opts, stream=None, check=True):
+    n = len(ctxs)
+    ca = (C.c_void_p * n)(*[c.value for c in ctxs])
+    ra = (C.c_void_p * n)(*[_dptr(t).value for t in rhss])
+    sa = (C.c_void_p * n)(*[_dptr(t).value for t in sols])
+    st = (eofa_solve_stats * n)()
+    s = lib().eofa_solve_batched(ca, n, ra, sa, C.byref(opts), st, _stream(stream))
+    if check:
+        _check(None, s)
+    return list(st)
+
+
+def eofa_destroy(ctx):
+    if ctx is not None and ctx.value:
+        lib().eofa_destroy(ctx)
+
+
+def eofa_status_string(s):
+    return lib().eofa_status_string(int(s)).decode()
+
+
+def eofa_hop_bytes(ctx, prec, with_local):
+    return float(lib().eofa_hop_bytes(ctx, int(prec), int(with_local)))
+
+
+class Solver:
+    """Context owner: Solver(gauge, dims, Ls, **action) then apply / solve."""
+
+    def __init__(self, gauge, dims, Ls, stream=None, **action):
+        import torch
+        if isinstance(gauge, np.ndarray):
+            gauge = torch.from_numpy(np.ascontiguousarray(gauge)).cuda()
+        self.params = make_params(dims, Ls, **action)
+        self.dims, self.Ls = tuple(dims), int(Ls)
+        self.ctx = eofa_create(self.params, gauge, stream)
+
+    @property
+    def shape5(self):
+        X, Y, Z, T = self.dims
+        return (T, Z, Y, X, self.Ls, 4, 3)
+
+    def _new(self):
+        import torch
+        return torch.empty(self.shape5, dtype=torch.complex128, device="cuda")
+
+    def apply(self, x, dag=False, stream=None):
+        out = self._new()
+        (eofa_apply_dag if dag else eofa_apply)(self.ctx, x, out, stream)
+        return out
+
+    def apply_h(self, x, stream=None):
+        out = self._new()
+        eofa_apply_h(self.ctx, x, out, stream)
+        return out
+
+    def solve(self, rhs, stream=None, out=None, check=True, **opts):
+        sol = self._new() if out is None else out
+        st = eofa_solve(self.ctx, rhs, sol, make_opts(**opts), stream, check=check)
+        return sol, st
+
+    def hop_bytes(self, prec, with_local):
+        return eofa_hop_bytes(self.ctx, prec, with_local)
+
+    def close(self):
+        eofa_destroy(self.ctx)
+        self.ctx = None
+
+    def __del__(self):
+        try:
+            if self.ctx is not None:
+                self.close()
+        except Exception:
+            pass

@@ -1,0 +1,359 @@
+// blas.cu -- Krylov vector updates with fused deterministic reductions,
+// precision conversions, and the layout import/export kernels between the
+// caller's canonical complex128 fields and the internal even-odd blocked
+// layout.  One thread per 5D site (xcb, s) of a half lattice.
+#include "blas.h"
+
+namespace eofa {
+
+constexpr int BT = 256;  // threads per block of every kernel in this file
+
+static inline int grid_for(long n) { return (int)((n + BT - 1) / BT); }
+
+// ---------------------------------------------------------------------------
+// scalars
+// ---------------------------------------------------------------------------
+__global__ void k_scal_init(DevScal* sc, double target_rr) {
+    sc->qq = sc->zz = sc->rr = sc->alpha = sc->beta = 0.0;
+    sc->target_rr = target_rr;
+    sc->iters = 0;
+    sc->done = 0;
+    sc->nonfinite = 0;
+}
+
+cudaError_t scal_init(DevScal* sc, double target_rr, cudaStream_t st) {
+    k_scal_init<<<1, 1, 0, st>>>(sc, target_rr);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// CG updates
+// ---------------------------------------------------------------------------
+template <typename S, typename SX>
+__global__ void __launch_bounds__(BT) k_cg_xr(VecRef x, VecRef p, VecRef q, VecRef r, long n5, int Ls,
+                                              Reduce rd, const int* done) {
+    typedef typename Traits<S>::R R;
+    typedef typename Traits<SX>::R RX;
+    if (*done) return;
+    const long t = (long)blockIdx.x * BT + threadIdx.x;
+    double nn = 0.0;
+    if (t < n5) {
+        const long xcb = t / Ls;
+        const int s = (int)(t - xcb * Ls);
+        const double al = rd.scal->alpha;
+        R pv[24], qv[24], rv[24];
+        RX xv[24];
+        load_sp<S, R>(p.d, p.n, xcb, s, Ls, pv);
+        load_sp<S, R>(q.d, q.n, xcb, s, Ls, qv);
+        load_sp<S, R>(r.d, r.n, xcb, s, Ls, rv);
+        load_sp<SX, RX>(x.d, x.n, xcb, s, Ls, xv);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) {
+            xv[i] += (RX)al * (RX)pv[i];
+            rv[i] -= (R)al * qv[i];
+            nn += (double)rv[i] * (double)rv[i];
+        }
+        store_sp<SX, RX>(x.d, x.n, xcb, s, Ls, xv);
+        store_sp<S, R>(r.d, r.n, xcb, s, Ls, rv);
+    }
+    block_reduce_finalize<BT>(nn, rd);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(BT) k_cg_p(VecRef p, VecRef z, long n5, int Ls, const DevScal* sc) {
+    typedef typename Traits<S>::R R;
+    if (sc->done) return;
+    const long t = (long)blockIdx.x * BT + threadIdx.x;
+    if (t >= n5) return;
+    const long xcb = t / Ls;
+    const int s = (int)(t - xcb * Ls);
+    const R be = (R)sc->beta;
+    R pv[24], zv[24];
+    load_sp<S, R>(p.d, p.n, xcb, s, Ls, pv);
+    load_sp<S, R>(z.d, z.n, xcb, s, Ls, zv);
+#pragma unroll
+    for (int i = 0; i < 24; ++i) pv[i] = zv[i] + be * pv[i];
+    store_sp<S, R>(p.d, p.n, xcb, s, Ls, pv);
+}
+
+// dst = a * src (types may differ); optional |dst|^2 reduction.
+// Scale: a = scale, or 1/sqrt(store[slot]) when inv_sqrt_slot >= 0.
+template <typename SD, typename SS>
+__global__ void __launch_bounds__(BT) k_copy(VecRef dst, VecRef src, long n5, int Ls, double scale,
+                                             int inv_sqrt_slot, Reduce rd) {
+    typedef typename Traits<SD>::R RD;
+    typedef typename Traits<SS>::R RS;
+    const long t = (long)blockIdx.x * BT + threadIdx.x;
+    double nn = 0.0;
+    if (t < n5) {
+        const long xcb = t / Ls;
+        const int s = (int)(t - xcb * Ls);
+        double a = scale;
+        if (inv_sqrt_slot >= 0) {
+            double v = rd.scal->store[inv_sqrt_slot];
+            a = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
+        }
+        RS sv[24];
+        RD dv[24];
+        load_sp<SS, RS>(src.d, src.n, xcb, s, Ls, sv);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) {
+            dv[i] = (RD)((double)sv[i] * a);
+            nn += (double)dv[i] * (double)dv[i];
+        }
+        store_sp<SD, RD>(dst.d, dst.n, xcb, s, Ls, dv);
+    }
+    if (rd.fin != FIN_NONE) block_reduce_finalize<BT>(nn, rd);
+}
+
+// x (FP64) += sqrt(store[slot]) * e  (defect-correction update)
+template <typename SE>
+__global__ void __launch_bounds__(BT) k_acc(VecRef x, VecRef e, long n5, int Ls, const DevScal* sc,
+                                            int slot) {
+    typedef typename Traits<SE>::R RE;
+    const long t = (long)blockIdx.x * BT + threadIdx.x;
+    if (t >= n5) return;
+    const long xcb = t / Ls;
+    const int s = (int)(t - xcb * Ls);
+    const double a = sqrt(sc->store[slot]);
+    double xv[24];
+    RE ev[24];
+    load_sp<double, double>(x.d, nullptr, xcb, s, Ls, xv);
+    load_sp<SE, RE>(e.d, e.n, xcb, s, Ls, ev);
+#pragma unroll
+    for (int i = 0; i < 24; ++i) xv[i] += a * (double)ev[i];
+    store_sp<double, double>(x.d, nullptr, xcb, s, Ls, xv);
+}
+
+// r = b - q (FP64), |r|^2 reduced
+__global__ void __launch_bounds__(BT) k_sub(VecRef r, VecRef b, VecRef q, long n5, int Ls, Reduce rd) {
+    const long t = (long)blockIdx.x * BT + threadIdx.x;
+    double nn = 0.0;
+    if (t < n5) {
+        const long xcb = t / Ls;
+        const int s = (int)(t - xcb * Ls);
+        double bv[24], qv[24];
+        load_sp<double, double>(b.d, nullptr, xcb, s, Ls, bv);
+        load_sp<double, double>(q.d, nullptr, xcb, s, Ls, qv);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) {
+            bv[i] -= qv[i];
+            nn += bv[i] * bv[i];
+        }
+        store_sp<double, double>(r.d, nullptr, xcb, s, Ls, bv);
+    }
+    block_reduce_finalize<BT>(nn, rd);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(BT) k_zero(VecRef v, long n5, int Ls) {
+    typedef typename Traits<S>::R R;
+    const long t = (long)blockIdx.x * BT + threadIdx.x;
+    if (t >= n5) return;
+    const long xcb = t / Ls;
+    const int s = (int)(t - xcb * Ls);
+    R z[24];
+#pragma unroll
+    for (int i = 0; i < 24; ++i) z[i] = (R)0;
+    store_sp<S, R>(v.d, v.n, xcb, s, Ls, z);
+}
+
+// ---------------------------------------------------------------------------
+// layout conversion: canonical complex128 <-> internal FP64, one parity
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long lex_of(const Geom& g, long xcb, int par) {
+    int rem = (int)xcb;
+    const int xh = rem % g.Xh; rem /= g.Xh;
+    const int y = rem % g.Y; rem /= g.Y;
+    const int z = rem % g.Z;
+    const int t = rem / g.Z;
+    const int x = 2 * xh + ((par + y + z + t) & 1);
+    return (((long)t * g.Z + z) * g.Y + y) * g.X + x;
+}
+
+// g5r5: read slice Ls-1-s and flip the sign of spins 2, 3 (gamma_5 R_5)
+__global__ void __launch_bounds__(BT) k_import(VecRef dst, const double* __restrict__ src, Geom g, int par,
+                                               int g5r5) {
+    const long t = (long)blockIdx.x * BT + threadIdx.x;
+    const long n5 = (long)g.Vh * g.Ls;
+    if (t >= n5) return;
+    const long xcb = t / g.Ls;
+    const int s = (int)(t - xcb * g.Ls);
+    const long lex = lex_of(g, xcb, par);
+    const int ss = g5r5 ? g.Ls - 1 - s : s;
+    const double2* p = reinterpret_cast<const double2*>(src) + (lex * g.Ls + ss) * 12;
+    double v[24];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        double2 q = p[c];
+        const double f = (g5r5 && c >= 6) ? -1.0 : 1.0;
+        v[2 * c] = f * q.x;
+        v[2 * c + 1] = f * q.y;
+    }
+    store_sp<double, double>(dst.d, nullptr, xcb, s, g.Ls, v);
+}
+
+__global__ void __launch_bounds__(BT) k_export(double* __restrict__ dst, VecRef src, Geom g, int par,
+                                               int g5r5) {
+    const long t = (long)blockIdx.x * BT + threadIdx.x;
+    const long n5 = (long)g.Vh * g.Ls;
+    if (t >= n5) return;
+    const long xcb = t / g.Ls;
+    const int s = (int)(t - xcb * g.Ls);
+    const long lex = lex_of(g, xcb, par);
+    double v[24];
+    load_sp<double, double>(src.d, nullptr, xcb, s, g.Ls, v);
+    const int ss = g5r5 ? g.Ls - 1 - s : s;
+    double2* p = reinterpret_cast<double2*>(dst) + (lex * g.Ls + ss) * 12;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        const double f = (g5r5 && c >= 6) ? -1.0 : 1.0;
+        p[c] = make_double2(f * v[2 * c], f * v[2 * c + 1]);
+    }
+}
+
+// gauge: canonical U[lex][mu][3][3] complex128 -> two-row links per parity in
+// all four storage precisions; flags links that are not SU(3) to 1e-10.
+__global__ void __launch_bounds__(BT) k_gauge(const double* __restrict__ U, Geom g, void* l64_0, void* l64_1,
+                                              void* l32_0, void* l32_1, void* l16_0, void* l16_1, void* lb_0,
+                                              void* lb_1, int* bad) {
+    const long t = (long)blockIdx.x * BT + threadIdx.x;
+    const long V = 2L * g.Vh;
+    if (t >= V * 4) return;
+    const long lex = t >> 2;
+    const int mu = (int)(t & 3);
+    int rem = (int)lex;
+    const int x = rem % g.X; rem /= g.X;
+    const int y = rem % g.Y; rem /= g.Y;
+    const int z = rem % g.Z;
+    const int tt = rem / g.Z;
+    const int par = (x + y + z + tt) & 1;
+    const long xcb = lex >> 1;
+    const double* u = U + (lex * 4 + mu) * 18;
+    // SU(3) check: rows orthonormal and row2 = conj(row0 x row1)
+    double dev = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double re = 0, im = 0;
+            for (int k = 0; k < 3; ++k) {
+                const double ar = u[(a * 3 + k) * 2], ai = u[(a * 3 + k) * 2 + 1];
+                const double br = u[(b * 3 + k) * 2], bi = u[(b * 3 + k) * 2 + 1];
+                re += ar * br + ai * bi;
+                im += ai * br - ar * bi;
+            }
+            dev = fmax(dev, fabs(re - (a == b ? 1.0 : 0.0)));
+            dev = fmax(dev, fabs(im));
+        }
+    {
+        const double* r0 = u;
+        const double* r1 = u + 6;
+        const double* r2 = u + 12;
+        for (int j = 0; j < 3; ++j) {
+            const int k = (j + 1) % 3, l = (j + 2) % 3;
+            const double cr = (r0[2 * k] * r1[2 * l] - r0[2 * k + 1] * r1[2 * l + 1]) -
+                              (r0[2 * l] * r1[2 * k] - r0[2 * l + 1] * r1[2 * k + 1]);
+            const double ci = (r0[2 * k] * r1[2 * l + 1] + r0[2 * k + 1] * r1[2 * l]) -
+                              (r0[2 * l] * r1[2 * k + 1] + r0[2 * l + 1] * r1[2 * k]);
+            dev = fmax(dev, fabs(r2[2 * j] - cr));
+            dev = fmax(dev, fabs(r2[2 * j + 1] + ci));
+        }
+    }
+    if (!(dev <= 1e-10)) atomicOr(bad, 1);
+    const long off = (xcb * 4 + mu) * 12;
+    double* d64 = reinterpret_cast<double*>(par ? l64_1 : l64_0) + off;
+    float* d32 = reinterpret_cast<float*>(par ? l32_1 : l32_0) + off;
+    __half* d16 = reinterpret_cast<__half*>(par ? l16_1 : l16_0) + off;
+    __nv_bfloat16* db = reinterpret_cast<__nv_bfloat16*>(par ? lb_1 : lb_0) + off;
+    for (int i = 0; i < 12; ++i) {
+        d64[i] = u[i];
+        d32[i] = (float)u[i];
+        d16[i] = __double2half(u[i]);
+        db[i] = __double2bfloat16(u[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host wrappers
+// ---------------------------------------------------------------------------
+template <typename F>
+static cudaError_t dispatch_prec(int prec, F&& f) {
+    switch (prec) {
+        case 0: return f((double*)nullptr);
+        case 1: return f((float*)nullptr);
+        case 2: return f((__half*)nullptr);
+        case 3: return f((__nv_bfloat16*)nullptr);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t blas_cg_xr(int prec, int xprec, VecRef x, VecRef p, VecRef q, VecRef r, long n5, int Ls,
+                       Reduce rd, const int* done, cudaStream_t st) {
+    return dispatch_prec(prec, [&](auto* tag) -> cudaError_t {
+        typedef std::remove_pointer_t<decltype(tag)> S;
+        if (xprec == 0) k_cg_xr<S, double><<<grid_for(n5), BT, 0, st>>>(x, p, q, r, n5, Ls, rd, done);
+        else k_cg_xr<S, float><<<grid_for(n5), BT, 0, st>>>(x, p, q, r, n5, Ls, rd, done);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t blas_cg_p(int prec, VecRef p, VecRef z, long n5, int Ls, const DevScal* sc, cudaStream_t st) {
+    return dispatch_prec(prec, [&](auto* tag) -> cudaError_t {
+        typedef std::remove_pointer_t<decltype(tag)> S;
+        k_cg_p<S><<<grid_for(n5), BT, 0, st>>>(p, z, n5, Ls, sc);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t blas_copy(int dprec, VecRef dst, int sprec, VecRef src, long n5, int Ls, double scale,
+                      int inv_sqrt_slot, Reduce rd, cudaStream_t st) {
+    return dispatch_prec(dprec, [&](auto* dtag) -> cudaError_t {
+        typedef std::remove_pointer_t<decltype(dtag)> SD;
+        return dispatch_prec(sprec, [&](auto* stag) -> cudaError_t {
+            typedef std::remove_pointer_t<decltype(stag)> SS;
+            k_copy<SD, SS><<<grid_for(n5), BT, 0, st>>>(dst, src, n5, Ls, scale, inv_sqrt_slot, rd);
+            return cudaGetLastError();
+        });
+    });
+}
+
+cudaError_t blas_acc(VecRef x, int eprec, VecRef e, long n5, int Ls, const DevScal* sc, int slot,
+                     cudaStream_t st) {
+    return dispatch_prec(eprec, [&](auto* tag) -> cudaError_t {
+        typedef std::remove_pointer_t<decltype(tag)> SE;
+        k_acc<SE><<<grid_for(n5), BT, 0, st>>>(x, e, n5, Ls, sc, slot);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t blas_sub(VecRef r, VecRef b, VecRef q, long n5, int Ls, Reduce rd, cudaStream_t st) {
+    k_sub<<<grid_for(n5), BT, 0, st>>>(r, b, q, n5, Ls, rd);
+    return cudaGetLastError();
+}
+
+cudaError_t blas_zero(int prec, VecRef v, long n5, int Ls, cudaStream_t st) {
+    return dispatch_prec(prec, [&](auto* tag) -> cudaError_t {
+        typedef std::remove_pointer_t<decltype(tag)> S;
+        k_zero<S><<<grid_for(n5), BT, 0, st>>>(v, n5, Ls);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t layout_import(VecRef dst, const double* src, const Geom& g, int par, int g5r5, cudaStream_t st) {
+    k_import<<<grid_for((long)g.Vh * g.Ls), BT, 0, st>>>(dst, src, g, par, g5r5);
+    return cudaGetLastError();
+}
+
+cudaError_t layout_export(double* dst, VecRef src, const Geom& g, int par, int g5r5, cudaStream_t st) {
+    k_export<<<grid_for((long)g.Vh * g.Ls), BT, 0, st>>>(dst, src, g, par, g5r5);
+    return cudaGetLastError();
+}
+
+cudaError_t gauge_import(const double* U, const Geom& g, void* const links[4][2], int* bad, cudaStream_t st) {
+    k_gauge<<<grid_for(2L * g.Vh * 4), BT, 0, st>>>(U, g, links[0][0], links[0][1], links[1][0], links[1][1],
+                                                    links[2][0], links[2][1], links[3][0], links[3][1], bad);
+    return cudaGetLastError();
+}
+
+int blas_max_grid(long n5) { return grid_for(n5); }
+
+}  // namespace eofa

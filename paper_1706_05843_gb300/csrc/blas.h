@@ -1,0 +1,39 @@
+// blas.h -- internal interface between the host driver (eofa.cu) and the
+// kernels of blas.cu and dslash_<prec>.cu.  Not part of the public ABI.
+#pragma once
+
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace eofa {
+
+struct VecRef {
+    void* d;    // chunk array of one parity
+    float* n;   // FP16 per-site scales (NULL otherwise)
+};
+
+struct HopArgs;
+
+// precision codes: 0 F64, 1 F32, 2 F16, 3 BF16 (the eofa_prec values)
+cudaError_t launch_hop_f64(int kind, const HopArgs& a, const void* coef, cudaStream_t st);
+cudaError_t launch_hop_f32(int kind, const HopArgs& a, const void* coef, cudaStream_t st);
+cudaError_t launch_hop_f16(int kind, const HopArgs& a, const void* coef, cudaStream_t st);
+cudaError_t launch_hop_bf16(int kind, const HopArgs& a, const void* coef, cudaStream_t st);
+
+cudaError_t scal_init(DevScal* sc, double target_rr, cudaStream_t st);
+cudaError_t blas_cg_xr(int prec, int xprec, VecRef x, VecRef p, VecRef q, VecRef r, long n5, int Ls,
+                       Reduce rd, const int* done, cudaStream_t st);
+cudaError_t blas_cg_p(int prec, VecRef p, VecRef z, long n5, int Ls, const DevScal* sc, cudaStream_t st);
+cudaError_t blas_copy(int dprec, VecRef dst, int sprec, VecRef src, long n5, int Ls, double scale,
+                      int inv_sqrt_slot, Reduce rd, cudaStream_t st);
+cudaError_t blas_acc(VecRef x, int eprec, VecRef e, long n5, int Ls, const DevScal* sc, int slot,
+                     cudaStream_t st);
+cudaError_t blas_sub(VecRef r, VecRef b, VecRef q, long n5, int Ls, Reduce rd, cudaStream_t st);
+cudaError_t blas_zero(int prec, VecRef v, long n5, int Ls, cudaStream_t st);
+cudaError_t layout_import(VecRef dst, const double* src, const Geom& g, int par, int g5r5, cudaStream_t st);
+cudaError_t layout_export(double* dst, VecRef src, const Geom& g, int par, int g5r5, cudaStream_t st);
+cudaError_t gauge_import(const double* U, const Geom& g, void* const links[4][2], int* bad, cudaStream_t st);
+int blas_max_grid(long n5);
+
+}  // namespace eofa

@@ -1,0 +1,506 @@
+// dslash.cuh -- the fused 4D Wilson hop + fifth-dimension kernel.
+//
+// One CTA owns NS output 4D sites of one checkerboard parity and all Ls
+// slices of them; thread (i, s) owns 5D site (x_i, s).  Three phases:
+//
+//  1. hop:   h(x, s) = sum_mu [ (1 - g gamma_mu) U_mu(x) chi(x+mu, s)
+//                             + (1 + g gamma_mu) U_mu(x-mu)^dag chi(x-mu, s) ]
+//            with g = +1 (D_h) or -1 (gamma_5 D_h gamma_5 = the hop of D^dag),
+//            chi = psi, or chi = D~ psi / b5 built on the fly from the
+//            neighbour's slices s-1 (P+ half) and s+1 (P- half) -- the
+//            "L acts first" order of Eq. (Ddwf).  Spin projection to half
+//            spinors, two-row links rebuilt in registers; h goes to shared
+//            memory.  An optional site-local input y is staged beside it.
+//  2. fifth dimension: each thread takes complex columns (x_i, spin, colour)
+//            and applies an O(Ls) program: the cyclic bidiagonal
+//            A = alpha + gamma L (the site-diagonal block of D_DWF, App. B),
+//            its transpose, its inverse by a closed-form corner plus a
+//            first-order recurrence, the rank-one EOFA shift u (x) v
+//            (Eqs. Mooee_shift_p/m) and its Sherman-Morrison inverse
+//            (Eq. sherman_morrison_mobius_inv), D~ = b5 + c5 L and D~^T.
+//  3. store: thread (i, s) writes its spinor back (coalesced 16-byte
+//            chunks) and contributes |out|^2 to a deterministic reduction.
+//
+// The kernel kinds below are the even-odd blocks of K (App. B):
+//   K_ee = K_oo = M (site-local), K_eo = K_oe = -1/2 D_h D~.
+#pragma once
+
+#include "common.cuh"
+
+namespace eofa {
+
+enum Kind {
+    KIND_EO_MINV = 0,      // out = -1/2 D~ M^-1 D_h D~ in            (Schur step 1)
+    KIND_OE_SCHUR = 1,     // out = M y + 1/2 D_h in                  (Schur step 2; in = D~ t)
+    KIND_EO_MINV_DAG = 2,  // out = -1/2 M^-T D~^T g5 D_h g5 in       (Schur^dag step 1)
+    KIND_OE_SCHUR_DAG = 3, // out = M^T y + 1/2 D~^T g5 D_h g5 in     (Schur^dag step 2)
+    KIND_RECON = 4,        // out = M^-1 (y + 1/2 D_h D~ in)          (even reconstruction)
+    KIND_SRC = 5,          // out = y + 1/2 D_h in                    (even-odd source)
+    KIND_FULL = 6,         // out = M y - 1/2 D_h D~ in               (K, one parity)
+    KIND_FULL_DAG = 7,     // out = M^T y - 1/2 D~^T g5 D_h g5 in     (K^dag, one parity)
+    KIND_LOC_DTMINV = 8,   // out = D~ M^-1 y
+    KIND_LOC_DT = 9,       // out = D~ y
+    KIND_LOC_DTINV = 10,   // out = D~^-1 y
+    NKIND = 11
+};
+
+template <int K> struct KindTraits {
+    static constexpr bool HOP = K <= KIND_FULL_DAG;
+    static constexpr bool DAG = K == KIND_EO_MINV_DAG || K == KIND_OE_SCHUR_DAG || K == KIND_FULL_DAG;
+    static constexpr bool PRE = K == KIND_EO_MINV || K == KIND_RECON || K == KIND_FULL;
+    static constexpr bool HASY = !(K == KIND_EO_MINV || K == KIND_EO_MINV_DAG);
+};
+
+struct HopArgs {
+    Geom g;
+    int out_par;
+    int pad;
+    const void* in;  const float* in_nrm;    // hop input, parity 1 - out_par
+    const void* y;   const float* y_nrm;     // site-local input, parity out_par
+    void* out;       float* out_nrm;         // output, parity out_par
+    const void* lk_out;                      // links of parity out_par
+    const void* lk_in;                       // links of parity 1 - out_par
+    Reduce rd;                               // rd.fin == FIN_NONE: no reduction
+    const int* done;                         // early exit when *done != 0 (may be NULL)
+};
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+template <typename R> struct C2 { R re, im; };
+
+template <typename R>
+__device__ __forceinline__ C2<R> cmul(C2<R> a, C2<R> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ C2<R> cmulc(C2<R> a, C2<R> b) {  // conj(a) * b
+    return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+
+// ---------------------------------------------------------------------------
+// one hopping direction: acc += phase (1 + SG gamma_MU) W chi, W = U or U^dag
+// u: 18 reals, rows 0..2 of the link (row 2 rebuilt).
+// ---------------------------------------------------------------------------
+template <typename R, int MU, int SG, bool ADJ>
+__device__ __forceinline__ void hop_dir(R* __restrict__ acc, const R* __restrict__ p,
+                                        const R* __restrict__ u, R phase) {
+    // spin projection: h = psi_up + SG B psi_dn, B = -i sigma_k (k = 1..3) or 1
+    R h[12];
+    constexpr R s = (R)SG;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const R p0r = p[0 * 6 + 2 * c], p0i = p[0 * 6 + 2 * c + 1];
+        const R p1r = p[1 * 6 + 2 * c], p1i = p[1 * 6 + 2 * c + 1];
+        const R p2r = p[2 * 6 + 2 * c], p2i = p[2 * 6 + 2 * c + 1];
+        const R p3r = p[3 * 6 + 2 * c], p3i = p[3 * 6 + 2 * c + 1];
+        R h0r, h0i, h1r, h1i;
+        if constexpr (MU == 0) {        // B psi_dn = (-i psi3, -i psi2)
+            h0r = p0r + s * p3i; h0i = p0i - s * p3r;
+            h1r = p1r + s * p2i; h1i = p1i - s * p2r;
+        } else if constexpr (MU == 1) { // B psi_dn = (-psi3, psi2)
+            h0r = p0r - s * p3r; h0i = p0i - s * p3i;
+            h1r = p1r + s * p2r; h1i = p1i + s * p2i;
+        } else if constexpr (MU == 2) { // B psi_dn = (-i psi2, i psi3)
+            h0r = p0r + s * p2i; h0i = p0i - s * p2r;
+            h1r = p1r - s * p3i; h1i = p1i + s * p3r;
+        } else {                        // B psi_dn = psi_dn
+            h0r = p0r + s * p2r; h0i = p0i + s * p2i;
+            h1r = p1r + s * p3r; h1i = p1i + s * p3i;
+        }
+        h[2 * c] = h0r; h[2 * c + 1] = h0i;
+        h[6 + 2 * c] = h1r; h[6 + 2 * c + 1] = h1i;
+    }
+    // colour: w = W h for both half-spinor components
+    R w[12];
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            C2<R> sum = {0, 0};
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                C2<R> hb = {h[sp * 6 + 2 * b], h[sp * 6 + 2 * b + 1]};
+                C2<R> t;
+                if constexpr (!ADJ) {
+                    C2<R> ua = {u[(a * 3 + b) * 2], u[(a * 3 + b) * 2 + 1]};
+                    t = cmul(ua, hb);
+                } else {
+                    C2<R> ub = {u[(b * 3 + a) * 2], u[(b * 3 + a) * 2 + 1]};
+                    t = cmulc(ub, hb);
+                }
+                sum.re += t.re;
+                sum.im += t.im;
+            }
+            w[sp * 6 + 2 * a] = sum.re * phase;
+            w[sp * 6 + 2 * a + 1] = sum.im * phase;
+        }
+    }
+    // reconstruct: upper += w, lower += SG B^dag w
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const R w0r = w[2 * c], w0i = w[2 * c + 1];
+        const R w1r = w[6 + 2 * c], w1i = w[6 + 2 * c + 1];
+        acc[0 * 6 + 2 * c] += w0r; acc[0 * 6 + 2 * c + 1] += w0i;
+        acc[1 * 6 + 2 * c] += w1r; acc[1 * 6 + 2 * c + 1] += w1i;
+        if constexpr (MU == 0) {        // B^dag w = (i w1, i w0)
+            acc[2 * 6 + 2 * c] -= s * w1i; acc[2 * 6 + 2 * c + 1] += s * w1r;
+            acc[3 * 6 + 2 * c] -= s * w0i; acc[3 * 6 + 2 * c + 1] += s * w0r;
+        } else if constexpr (MU == 1) { // B^dag w = (w1, -w0)
+            acc[2 * 6 + 2 * c] += s * w1r; acc[2 * 6 + 2 * c + 1] += s * w1i;
+            acc[3 * 6 + 2 * c] -= s * w0r; acc[3 * 6 + 2 * c + 1] -= s * w0i;
+        } else if constexpr (MU == 2) { // B^dag w = (i w0, -i w1)
+            acc[2 * 6 + 2 * c] -= s * w0i; acc[2 * 6 + 2 * c + 1] += s * w0r;
+            acc[3 * 6 + 2 * c] += s * w1i; acc[3 * 6 + 2 * c + 1] -= s * w1r;
+        } else {                        // B^dag w = w
+            acc[2 * 6 + 2 * c] += s * w0r; acc[2 * 6 + 2 * c + 1] += s * w0i;
+            acc[3 * 6 + 2 * c] += s * w1r; acc[3 * 6 + 2 * c + 1] += s * w1i;
+        }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void rebuild_row2(R* u) {
+    // row2 = conj(row0 x row1)
+    C2<R> a0 = {u[0], u[1]}, a1 = {u[2], u[3]}, a2 = {u[4], u[5]};
+    C2<R> b0 = {u[6], u[7]}, b1 = {u[8], u[9]}, b2 = {u[10], u[11]};
+    C2<R> c0 = cmul(a1, b2), d0 = cmul(a2, b1);
+    C2<R> c1 = cmul(a2, b0), d1 = cmul(a0, b2);
+    C2<R> c2 = cmul(a0, b1), d2 = cmul(a1, b0);
+    u[12] = c0.re - d0.re; u[13] = -(c0.im - d0.im);
+    u[14] = c1.re - d1.re; u[15] = -(c1.im - d1.im);
+    u[16] = c2.re - d2.re; u[17] = -(c2.im - d2.im);
+}
+
+// ---------------------------------------------------------------------------
+// fifth-dimension column operators (mirrored coordinates: always L+ / L-)
+// ---------------------------------------------------------------------------
+// (a + g L+) v,  L+: v_s <- v_{s-1}, v_0 <- -m v_{Ls-1}
+template <typename R, int LS>
+__device__ __forceinline__ void op_fwd(C2<R>* v, R a, R g, R mg) {
+    C2<R> last = v[LS - 1];
+#pragma unroll
+    for (int s = LS - 1; s >= 1; --s) {
+        v[s].re = a * v[s].re + g * v[s - 1].re;
+        v[s].im = a * v[s].im + g * v[s - 1].im;
+    }
+    v[0].re = a * v[0].re - mg * last.re;
+    v[0].im = a * v[0].im - mg * last.im;
+}
+// (a + g L-) v = (a + g L+^T) v
+template <typename R, int LS>
+__device__ __forceinline__ void op_fwdT(C2<R>* v, R a, R g, R mg) {
+    C2<R> first = v[0];
+#pragma unroll
+    for (int s = 0; s < LS - 1; ++s) {
+        v[s].re = a * v[s].re + g * v[s + 1].re;
+        v[s].im = a * v[s].im + g * v[s + 1].im;
+    }
+    v[LS - 1].re = a * v[LS - 1].re - mg * first.re;
+    v[LS - 1].im = a * v[LS - 1].im - mg * first.im;
+}
+// solve (a + g L+) t = v in place: t_{Ls-1} = sum_j w_j v_{Ls-1-j},
+// t_0 = v_0/a + m z t_{Ls-1}, t_s = v_s/a - z t_{s-1}.
+template <typename R, int LS>
+__device__ __forceinline__ void op_inv(C2<R>* v, R ia, R z, R mz, const R* w) {
+    C2<R> tl = {0, 0};
+#pragma unroll
+    for (int j = 0; j < LS; ++j) {
+        tl.re += w[j] * v[LS - 1 - j].re;
+        tl.im += w[j] * v[LS - 1 - j].im;
+    }
+    v[0].re = ia * v[0].re + mz * tl.re;
+    v[0].im = ia * v[0].im + mz * tl.im;
+#pragma unroll
+    for (int s = 1; s < LS - 1; ++s) {
+        v[s].re = ia * v[s].re - z * v[s - 1].re;
+        v[s].im = ia * v[s].im - z * v[s - 1].im;
+    }
+    v[LS - 1] = tl;
+}
+// solve (a + g L-) t = v in place (the mirror image of op_inv)
+template <typename R, int LS>
+__device__ __forceinline__ void op_invT(C2<R>* v, R ia, R z, R mz, const R* w) {
+    C2<R> t0 = {0, 0};
+#pragma unroll
+    for (int j = 0; j < LS; ++j) {
+        t0.re += w[j] * v[j].re;
+        t0.im += w[j] * v[j].im;
+    }
+    v[LS - 1].re = ia * v[LS - 1].re + mz * t0.re;
+    v[LS - 1].im = ia * v[LS - 1].im + mz * t0.im;
+#pragma unroll
+    for (int s = LS - 2; s >= 1; --s) {
+        v[s].re = ia * v[s].re - z * v[s + 1].re;
+        v[s].im = ia * v[s].im - z * v[s + 1].im;
+    }
+    v[0] = t0;
+}
+
+// M = A + pm beta u (x) v  on the shift chirality
+template <typename R, int LS>
+__device__ __forceinline__ void op_M(C2<R>* v, const SCoef<R>& c, bool sh) {
+    C2<R> vl = v[LS - 1];
+    op_fwd<R, LS>(v, c.alpha, c.gamma, c.m * c.gamma);
+    if (sh) {
+#pragma unroll
+        for (int s = 0; s < LS; ++s) {
+            R f = c.sbk * c.um[s];
+            v[s].re += f * vl.re;
+            v[s].im += f * vl.im;
+        }
+    }
+}
+template <typename R, int LS>
+__device__ __forceinline__ void op_MT(C2<R>* v, const SCoef<R>& c, bool sh) {
+    C2<R> d = {0, 0};
+    if (sh) {
+#pragma unroll
+        for (int s = 0; s < LS; ++s) {
+            d.re += c.um[s] * v[s].re;
+            d.im += c.um[s] * v[s].im;
+        }
+    }
+    op_fwdT<R, LS>(v, c.alpha, c.gamma, c.m * c.gamma);
+    if (sh) {
+        v[LS - 1].re += c.sbk * d.re;
+        v[LS - 1].im += c.sbk * d.im;
+    }
+}
+// Sherman-Morrison: M^-1 v = A^-1 v - (pm beta k (A^-1 v)_{j*} / den) x
+template <typename R, int LS>
+__device__ __forceinline__ void op_Minv(C2<R>* v, const SCoef<R>& c, bool sh) {
+    op_inv<R, LS>(v, c.ia, c.za, c.mza, c.wa);
+    if (sh) {
+        C2<R> t = {c.sbk_den * v[LS - 1].re, c.sbk_den * v[LS - 1].im};
+#pragma unroll
+        for (int s = 0; s < LS; ++s) {
+            v[s].re -= c.xm[s] * t.re;
+            v[s].im -= c.xm[s] * t.im;
+        }
+    }
+}
+// M^-T v = A^-T v - (pm beta (u . A^-T v) / den) y
+template <typename R, int LS>
+__device__ __forceinline__ void op_MinvT(C2<R>* v, const SCoef<R>& c, bool sh) {
+    op_invT<R, LS>(v, c.ia, c.za, c.mza, c.wa);
+    if (sh) {
+        C2<R> d = {0, 0};
+#pragma unroll
+        for (int s = 0; s < LS; ++s) {
+            d.re += c.um[s] * v[s].re;
+            d.im += c.um[s] * v[s].im;
+        }
+        d.re *= c.sb_den;
+        d.im *= c.sb_den;
+#pragma unroll
+        for (int s = 0; s < LS; ++s) {
+            v[s].re -= c.ym[s] * d.re;
+            v[s].im -= c.ym[s] * d.im;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
+template <typename R> struct ShStride;
+template <> struct ShStride<float> { static constexpr int V = 28; };   // 112 B rows: conflict-free float4
+template <> struct ShStride<double> { static constexpr int V = 26; };  // 208 B rows: conflict-free double2
+
+template <int LS> struct Tile {
+    static constexpr int NS = (LS >= 16) ? 8 : (LS == 12 ? 16 : 128 / LS);
+    static constexpr int NT = NS * LS;
+};
+
+template <typename S, int LS, int KIND>
+__global__ void __launch_bounds__(Tile<LS>::NT)
+hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
+    typedef typename Traits<S>::R R;
+    typedef KindTraits<KIND> KT;
+    constexpr int NS = Tile<LS>::NS;
+    constexpr int NT = Tile<LS>::NT;
+    constexpr int ST = ShStride<R>::V;
+
+    if (a.done && *a.done) return;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* sh = reinterpret_cast<R*>(smem_raw);          // [NS*LS][ST] hop result
+    R* sy = sh + NS * LS * ST;                        // [NS*LS][ST] local input
+
+    const int tid = threadIdx.x;
+    const int il = tid / LS;
+    const int s = tid - il * LS;
+    const long xcb = (long)blockIdx.x * NS + il;
+    const bool valid = xcb < a.g.Vh;
+    const int row = il * LS + s;
+
+    // ---------------- phase 1: hop and staging --------------------------
+    if (valid) {
+        if constexpr (KT::HOP) {
+            const Geom& g = a.g;
+            int rem = (int)xcb;
+            const int xh = rem % g.Xh; rem /= g.Xh;
+            const int y = rem % g.Y; rem /= g.Y;
+            const int z = rem % g.Z;
+            const int t = rem / g.Z;
+            const int x = 2 * xh + ((a.out_par + y + z + t) & 1);
+            const int co[4] = {x, y, z, t};
+            const int dm[4] = {g.X, g.Y, g.Z, g.T};
+            R acc[24];
+#pragma unroll
+            for (int i = 0; i < 24; ++i) acc[i] = (R)0;
+            constexpr int FS = KT::DAG ? +1 : -1;  // forward projector 1 + FS gamma
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+                for (int dir = 0; dir < 2; ++dir) {
+                    int cn[4] = {co[0], co[1], co[2], co[3]};
+                    R ph = (R)1;
+                    if (dir == 0) {
+                        cn[mu] = (co[mu] + 1 == dm[mu]) ? 0 : co[mu] + 1;
+                        if (mu == 3 && co[3] == dm[3] - 1) ph = (R)g.tbc;
+                    } else {
+                        cn[mu] = (co[mu] == 0) ? dm[mu] - 1 : co[mu] - 1;
+                        if (mu == 3 && co[3] == 0) ph = (R)g.tbc;
+                    }
+                    const long ncb = ((((long)cn[3] * g.Z + cn[2]) * g.Y + cn[1]) * g.X + cn[0]) >> 1;
+                    R p[24];
+                    load_sp<S, R>(a.in, a.in_nrm, ncb, s, LS, p);
+                    if constexpr (KT::PRE) {
+                        // chi = psi + (c5/b5) L psi (the b5 factor is applied in phase 2)
+                        R q[12];
+                        const int sm = (s == 0) ? LS - 1 : s - 1;
+                        const R fu = (s == 0) ? -cf.mzb : cf.zb;
+                        load_half<S, R>(a.in, a.in_nrm, ncb, sm, LS, 0, q);
+#pragma unroll
+                        for (int i = 0; i < 12; ++i) p[i] += fu * q[i];
+                        const int sp = (s == LS - 1) ? 0 : s + 1;
+                        const R fd = (s == LS - 1) ? -cf.mzb : cf.zb;
+                        load_half<S, R>(a.in, a.in_nrm, ncb, sp, LS, 1, q);
+#pragma unroll
+                        for (int i = 0; i < 12; ++i) p[12 + i] += fd * q[i];
+                    }
+                    R u[18];
+                    if (dir == 0) load_link<S, R>(a.lk_out, xcb, mu, u);
+                    else load_link<S, R>(a.lk_in, ncb, mu, u);
+                    rebuild_row2(u);
+                    if (dir == 0) {
+                        if (mu == 0) hop_dir<R, 0, FS, false>(acc, p, u, ph);
+                        if (mu == 1) hop_dir<R, 1, FS, false>(acc, p, u, ph);
+                        if (mu == 2) hop_dir<R, 2, FS, false>(acc, p, u, ph);
+                        if (mu == 3) hop_dir<R, 3, FS, false>(acc, p, u, ph);
+                    } else {
+                        if (mu == 0) hop_dir<R, 0, -FS, true>(acc, p, u, ph);
+                        if (mu == 1) hop_dir<R, 1, -FS, true>(acc, p, u, ph);
+                        if (mu == 2) hop_dir<R, 2, -FS, true>(acc, p, u, ph);
+                        if (mu == 3) hop_dir<R, 3, -FS, true>(acc, p, u, ph);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 24; ++i) sh[row * ST + i] = acc[i];
+        }
+        if constexpr (KT::HASY) {
+            R v[24];
+            load_sp<S, R>(a.y, a.y_nrm, xcb, s, LS, v);
+#pragma unroll
+            for (int i = 0; i < 24; ++i) sy[row * ST + i] = v[i];
+        }
+    }
+    __syncthreads();
+
+    // ---------------- phase 2: fifth-dimension program ------------------
+    // scale of the hop term (the b5 of the on-the-fly D~ folded in)
+    const R hb = KT::PRE ? cf.b5 : (R)1;
+    for (int col = tid; col < NS * 12; col += NT) {
+        const int ci = col / 12;
+        const int cc = col - ci * 12;        // spin * 3 + colour
+        const int chi = cc >= 6 ? 1 : 0;     // 0: P+, 1: P-
+        const bool shv = cf.has_shift && (chi == cf.cs);
+        const int base = ci * LS;
+        C2<R> v[LS];
+        if constexpr (KIND == KIND_EO_MINV) {
+#pragma unroll
+            for (int k = 0; k < LS; ++k) {
+                const int r = base + (chi ? LS - 1 - k : k);
+                v[k] = {sh[r * ST + 2 * cc], sh[r * ST + 2 * cc + 1]};
+            }
+            op_Minv<R, LS>(v, cf, shv);
+            op_fwd<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
+            const R f = (R)(-0.5) * hb;
+#pragma unroll
+            for (int k = 0; k < LS; ++k) { v[k].re *= f; v[k].im *= f; }
+        } else if constexpr (KIND == KIND_EO_MINV_DAG) {
+#pragma unroll
+            for (int k = 0; k < LS; ++k) {
+                const int r = base + (chi ? LS - 1 - k : k);
+                v[k] = {sh[r * ST + 2 * cc], sh[r * ST + 2 * cc + 1]};
+            }
+            op_fwdT<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
+            op_MinvT<R, LS>(v, cf, shv);
+#pragma unroll
+            for (int k = 0; k < LS; ++k) { v[k].re *= (R)-0.5; v[k].im *= (R)-0.5; }
+        } else {
+#pragma unroll
+            for (int k = 0; k < LS; ++k) {
+                const int r = base + (chi ? LS - 1 - k : k);
+                v[k] = {sy[r * ST + 2 * cc], sy[r * ST + 2 * cc + 1]};
+            }
+            if constexpr (KIND == KIND_OE_SCHUR || KIND == KIND_FULL) op_M<R, LS>(v, cf, shv);
+            if constexpr (KIND == KIND_OE_SCHUR_DAG || KIND == KIND_FULL_DAG) op_MT<R, LS>(v, cf, shv);
+            if constexpr (KT::HOP) {
+                C2<R> w[LS];
+#pragma unroll
+                for (int k = 0; k < LS; ++k) {
+                    const int r = base + (chi ? LS - 1 - k : k);
+                    w[k] = {sh[r * ST + 2 * cc], sh[r * ST + 2 * cc + 1]};
+                }
+                if constexpr (KIND == KIND_OE_SCHUR_DAG || KIND == KIND_FULL_DAG)
+                    op_fwdT<R, LS>(w, cf.b5, cf.c5, cf.m * cf.c5);
+                const R f = ((KIND == KIND_FULL || KIND == KIND_FULL_DAG) ? (R)-0.5 : (R)0.5) * hb;
+#pragma unroll
+                for (int k = 0; k < LS; ++k) {
+                    v[k].re += f * w[k].re;
+                    v[k].im += f * w[k].im;
+                }
+            }
+            if constexpr (KIND == KIND_RECON) op_Minv<R, LS>(v, cf, shv);
+            if constexpr (KIND == KIND_LOC_DTMINV) {
+                op_Minv<R, LS>(v, cf, shv);
+                op_fwd<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
+            }
+            if constexpr (KIND == KIND_LOC_DT) op_fwd<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
+            if constexpr (KIND == KIND_LOC_DTINV) op_inv<R, LS>(v, cf.ib, cf.zb, cf.mzb, cf.wb);
+        }
+#pragma unroll
+        for (int k = 0; k < LS; ++k) {
+            const int r = base + (chi ? LS - 1 - k : k);
+            sh[r * ST + 2 * cc] = v[k].re;
+            sh[r * ST + 2 * cc + 1] = v[k].im;
+        }
+    }
+    __syncthreads();
+
+    // ---------------- phase 3: store + reduction ------------------------
+    double nn = 0.0;
+    if (valid) {
+        R v[24];
+#pragma unroll
+        for (int i = 0; i < 24; ++i) v[i] = sh[row * ST + i];
+        store_sp<S, R>(a.out, a.out_nrm, xcb, s, LS, v);
+        if (a.rd.fin != FIN_NONE) {
+#pragma unroll
+            for (int i = 0; i < 24; ++i) nn += (double)v[i] * (double)v[i];
+        }
+    }
+    if (a.rd.fin != FIN_NONE) block_reduce_finalize<NT>(nn, a.rd);
+}
+
+template <typename S, int LS>
+constexpr size_t hop_smem_bytes() {
+    typedef typename Traits<S>::R R;
+    return 2ull * Tile<LS>::NT * ShStride<R>::V * sizeof(R);
+}
+
+}  // namespace eofa

@@ -1,0 +1,652 @@
+// eofa.cu -- host driver and C ABI of the GB300 EOFA solver (see eofa.h).
+//
+// Solve path (App. B of arXiv:1706.05843):
+//   b   = g5 R5 phi (H form) or b (K form), imported into the even-odd layout
+//   b~o = b_o - K_oe K_ee^-1 b_e                       even-odd source
+//   CGNR on S = K_oo - K_oe K_ee^-1 K_eo:  S^dag S x_o = S^dag b~o
+//     inside a restarted defect-correction loop (Sec. V.A): the FP64 outer
+//     loop forms r = b~o - S x_o, the inner CGNR solves S e = r/|r| in the
+//     requested storage precision, x_o += |r| e
+//   x_e = K_ee^-1 (b_e - K_eo x_o)                     reconstruction
+//   psi = D~(m1) psi'                                  undo the Cayley form
+//   true residual ||b - K psi'|| / ||b|| in FP64
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "blas.h"
+#include "dslash.cuh"
+#include "eofa.h"
+
+using namespace eofa;
+
+namespace {
+
+struct Inner {
+    bool ready = false;
+    VecRef r{}, p{}, q{}, z{}, t{}, x{};
+};
+
+}  // namespace
+
+struct eofa_ctx {
+    eofa_params p;
+    Geom g;
+    long n5 = 0;
+    SCoef<double> c64;
+    SCoef<float> c32;
+    void* links[4][2] = {};
+    VecRef b[2]{}, x[2]{}, t[2]{}, ro{}, bto{}, qo{};
+    Inner inner[4];
+    double* partials = nullptr;
+    unsigned* counter = nullptr;
+    DevScal* scal = nullptr;
+    DevScal* h_scal = nullptr;  // pinned
+    int* d_flag = nullptr;
+    std::vector<void*> allocs;
+    std::string err;
+    // hop-kernel timing
+    bool timing = false;
+    std::vector<cudaEvent_t> evs;
+    int ev_used = 0;
+    double hop_ms = 0.0;
+    int hop_launches = 0;
+    double hop_bytes = 0.0;
+    std::vector<double> ev_bytes;
+    long launches = 0;  // kernels launched since the last reset
+};
+
+namespace {
+
+const int kWidth[4] = {8, 4, 2, 2};
+
+eofa_status fail(eofa_ctx* c, eofa_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+eofa_status cuda_fail(eofa_ctx* c, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    if (c) c->err = m;
+    return e == cudaErrorMemoryAllocation ? EOFA_ERR_OOM : EOFA_ERR_CUDA;
+}
+
+#define CK(call, where)                                          \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where);   \
+    } while (0)
+
+// CK for calls that launch exactly one kernel
+#define CKL(call, where)                                         \
+    do {                                                         \
+        CK(call, where);                                         \
+        ++c->launches;                                           \
+    } while (0)
+
+eofa_status dalloc(eofa_ctx* c, void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(c, e, "cudaMalloc");
+    }
+    c->allocs.push_back(*p);
+    return EOFA_OK;
+}
+
+eofa_status vec_alloc(eofa_ctx* c, int prec, VecRef* v) {
+    eofa_status s = dalloc(c, &v->d, (size_t)c->n5 * 24 * kWidth[prec]);
+    if (s != EOFA_OK) return s;
+    v->n = nullptr;
+    if (prec == EOFA_F16) {
+        void* n = nullptr;
+        s = dalloc(c, &n, (size_t)c->n5 * sizeof(float));
+        if (s != EOFA_OK) return s;
+        v->n = (float*)n;
+    }
+    return EOFA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// fifth-dimension coefficients (host, FP64)
+// ---------------------------------------------------------------------------
+// solve (a + g L+) t = v, L+ with mass m (mirrored coordinates)
+void host_inv(int Ls, double a, double g, double m, const double* v, double* t) {
+    const double z = g / a;
+    const double den = a * (1.0 + m * std::pow(z, Ls));
+    double tl = 0.0, w = 1.0;
+    for (int j = 0; j < Ls; ++j) {
+        tl += w * v[Ls - 1 - j] / den;
+        w *= -z;
+    }
+    t[0] = v[0] / a + m * z * tl;
+    for (int s = 1; s < Ls - 1; ++s) t[s] = v[s] / a - z * t[s - 1];
+    t[Ls - 1] = tl;
+}
+// solve (a + g L-) t = v
+void host_invT(int Ls, double a, double g, double m, const double* v, double* t) {
+    std::vector<double> vr(Ls), tr(Ls);
+    for (int s = 0; s < Ls; ++s) vr[s] = v[Ls - 1 - s];
+    host_inv(Ls, a, g, m, vr.data(), tr.data());
+    for (int s = 0; s < Ls; ++s) t[s] = tr[Ls - 1 - s];
+}
+
+template <typename R>
+void cast_coef(const SCoef<double>& d, SCoef<R>& r) {
+    r.alpha = (R)d.alpha; r.gamma = (R)d.gamma; r.b5 = (R)d.b5; r.c5 = (R)d.c5; r.m = (R)d.m;
+    r.ia = (R)d.ia; r.za = (R)d.za; r.mza = (R)d.mza;
+    r.ib = (R)d.ib; r.zb = (R)d.zb; r.mzb = (R)d.mzb;
+    r.sbk = (R)d.sbk; r.sbk_den = (R)d.sbk_den; r.sb_den = (R)d.sb_den;
+    r.cs = d.cs; r.has_shift = d.has_shift;
+    for (int i = 0; i < LSMAX; ++i) {
+        r.wa[i] = (R)d.wa[i]; r.wb[i] = (R)d.wb[i];
+        r.um[i] = (R)d.um[i]; r.xm[i] = (R)d.xm[i]; r.ym[i] = (R)d.ym[i];
+    }
+}
+
+// App. B: A = (D_DWF)_ee = alpha + gamma L(m1), alpha = b5 (4 - M5) + 1,
+// gamma = c5 (4 - M5) - 1; the shift u_pm (x) v_pm with the closed forms of
+// u_pm (mass m1) and v_pm = k(m2, m3) e_{Ls-1 | 0}; Sherman-Morrison vectors
+// x = A^-1 u (the tridiagonal-algorithm step of App. B) and y = A^-T v.
+eofa_status build_coef(eofa_ctx* c) {
+    const eofa_params& p = c->p;
+    const int Ls = p.Ls;
+    SCoef<double>& k = c->c64;
+    std::memset(&k, 0, sizeof(k));
+    const double b5 = p.b, c5 = p.c, m = p.m1;
+    if (b5 == 0.0) return fail(c, EOFA_ERR_UNSUPPORTED, "b (b5) must be non-zero");
+    const double alpha = b5 * (4.0 - p.M5) + 1.0;
+    const double gamma = c5 * (4.0 - p.M5) - 1.0;
+    if (alpha == 0.0) return fail(c, EOFA_ERR_SINGULAR, "b5 (4 - M5) + 1 = 0");
+    const double za = gamma / alpha, zb = c5 / b5;
+    if (std::fabs(za) >= 1.0 || std::fabs(zb) >= 1.0)
+        return fail(c, EOFA_ERR_UNSUPPORTED,
+                    "fifth-dimension recurrences need |(c5(4-M5)-1)/(b5(4-M5)+1)| < 1 and |c5/b5| < 1");
+    const double ca = 1.0 + m * std::pow(za, Ls), cb = 1.0 + m * std::pow(zb, Ls);
+    if (std::fabs(ca) < 1e-14 || std::fabs(cb) < 1e-14)
+        return fail(c, EOFA_ERR_SINGULAR, "cyclic fifth-dimension block is singular");
+    auto N = [&](double mm) { return std::pow(b5, Ls) + mm * std::pow(c5, Ls); };
+    if (N(p.m1) == 0.0 || N(p.m2) == 0.0 || N(p.m3) == 0.0)
+        return fail(c, EOFA_ERR_SINGULAR, "N(m) = b5^Ls + m c5^Ls vanishes");
+    k.alpha = alpha; k.gamma = gamma; k.b5 = b5; k.c5 = c5; k.m = m;
+    k.ia = 1.0 / alpha; k.za = za; k.mza = m * za;
+    k.ib = 1.0 / b5; k.zb = zb; k.mzb = m * zb;
+    double wa = 1.0, wb = 1.0;
+    for (int j = 0; j < Ls; ++j) {
+        k.wa[j] = wa / (alpha * ca);
+        k.wb[j] = wb / (b5 * cb);
+        wa *= -za;
+        wb *= -zb;
+    }
+    // k(m2, m3) = 2c (m3 - m2) (c+d)^{2Ls} / (N(m2) N(m3)), 2c = b5 + c5
+    const double kk = (b5 + c5) * (p.m3 - p.m2) * std::pow(b5, 2 * Ls) / (N(p.m2) * N(p.m3));
+    const double N1 = N(p.m1);
+    std::vector<double> u(Ls);
+    for (int s = 0; s < Ls; ++s) {
+        if (p.pm > 0)
+            u[s] = ((s & 1) ? -1.0 : 1.0) * std::pow(c5, s) / std::pow(b5, Ls + s + 1) * N1;
+        else
+            u[s] = ((s & 1) ? 1.0 : -1.0) * std::pow(c5, Ls - 1 - s) / std::pow(b5, 2 * Ls - s) * N1;
+    }
+    k.cs = p.pm > 0 ? 0 : 1;
+    for (int s = 0; s < Ls; ++s) k.um[s] = (k.cs == 0) ? u[s] : u[Ls - 1 - s];
+    host_inv(Ls, alpha, gamma, m, k.um, k.xm);
+    std::vector<double> e(Ls, 0.0);
+    e[Ls - 1] = kk;
+    host_invT(Ls, alpha, gamma, m, e.data(), k.ym);
+    k.has_shift = p.beta != 0.0;
+    const double sb = p.pm * p.beta;
+    const double den = 1.0 + sb * kk * k.xm[Ls - 1];
+    if (k.has_shift && std::fabs(den) < 1e-14)
+        return fail(c, EOFA_ERR_SINGULAR, "Sherman-Morrison denominator 1 + pm beta <v, A^-1 u> ~ 0");
+    k.sbk = sb * kk;
+    k.sbk_den = k.has_shift ? sb * kk / den : 0.0;
+    k.sb_den = k.has_shift ? sb / den : 0.0;
+    cast_coef(k, c->c32);
+    return EOFA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernel helpers
+// ---------------------------------------------------------------------------
+Reduce red(eofa_ctx* c, int fin, int slot = 0) {
+    Reduce r;
+    r.partials = c->partials;
+    r.counter = c->counter;
+    r.scal = c->scal;
+    r.fin = fin;
+    r.slot = slot;
+    return r;
+}
+
+double hop_bytes_of(const eofa_ctx* c, int prec, int with_local) {
+    const double w = kWidth[prec];
+    double per5 = (48.0 + (with_local ? 24.0 : 0.0)) * w;
+    if (prec == EOFA_F16) per5 += 4.0 * (2 + (with_local ? 1 : 0));
+    return c->n5 * per5 + (double)c->g.Vh * 8.0 * 12.0 * w;
+}
+
+eofa_status hop(eofa_ctx* c, int prec, int kind, int out_par, VecRef in, VecRef y, VecRef out, Reduce rd,
+                const int* done, cudaStream_t st, bool timed = false) {
+    HopArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = c->g;
+    a.out_par = out_par;
+    a.in = in.d; a.in_nrm = in.n;
+    a.y = y.d; a.y_nrm = y.n;
+    a.out = out.d; a.out_nrm = out.n;
+    a.lk_out = c->links[prec][out_par];
+    a.lk_in = c->links[prec][1 - out_par];
+    a.rd = rd;
+    a.done = done;
+    const void* coef = prec == EOFA_F64 ? (const void*)&c->c64 : (const void*)&c->c32;
+    const bool tm = timed && c->timing;
+    if (tm) {
+        if (c->ev_used + 2 > (int)c->evs.size()) {
+            for (int i = 0; i < 64; ++i) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e), "cudaEventCreate");
+                c->evs.push_back(e);
+            }
+        }
+        CK(cudaEventRecord(c->evs[c->ev_used], st), "cudaEventRecord");
+    }
+    cudaError_t e;
+    switch (prec) {
+        case EOFA_F64: e = launch_hop_f64(kind, a, coef, st); break;
+        case EOFA_F32: e = launch_hop_f32(kind, a, coef, st); break;
+        case EOFA_F16: e = launch_hop_f16(kind, a, coef, st); break;
+        default: e = launch_hop_bf16(kind, a, coef, st); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "hop kernel launch");
+    ++c->launches;
+    if (tm) {
+        CK(cudaEventRecord(c->evs[c->ev_used + 1], st), "cudaEventRecord");
+        const bool wl = kind == KIND_OE_SCHUR || kind == KIND_OE_SCHUR_DAG;
+        if ((int)c->ev_bytes.size() < c->ev_used / 2 + 1) c->ev_bytes.resize(c->ev_used / 2 + 1);
+        c->ev_bytes[c->ev_used / 2] = hop_bytes_of(c, prec, wl);
+        c->ev_used += 2;
+    }
+    return EOFA_OK;
+}
+
+// after a stream synchronisation: fold the recorded hop timings into the totals
+eofa_status drain_timers(eofa_ctx* c) {
+    for (int i = 0; i + 1 < c->ev_used; i += 2) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->evs[i], c->evs[i + 1]), "cudaEventElapsedTime");
+        c->hop_ms += ms;
+        c->hop_launches += 1;
+        c->hop_bytes += c->ev_bytes[i / 2];
+    }
+    c->ev_used = 0;
+    return EOFA_OK;
+}
+
+eofa_status read_scal(eofa_ctx* c, cudaStream_t st) {
+    CK(cudaMemcpyAsync(c->h_scal, c->scal, sizeof(DevScal), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    return drain_timers(c);
+}
+
+eofa_status ensure_inner(eofa_ctx* c, int P) {
+    Inner& in = c->inner[P];
+    if (in.ready) return EOFA_OK;
+    eofa_status s;
+    if ((s = vec_alloc(c, P, &in.r)) || (s = vec_alloc(c, P, &in.p)) || (s = vec_alloc(c, P, &in.q)) ||
+        (s = vec_alloc(c, P, &in.z)) || (s = vec_alloc(c, P, &in.t)) ||
+        (s = vec_alloc(c, P == EOFA_F64 ? EOFA_F64 : EOFA_F32, &in.x)))
+        return s;
+    in.ready = true;
+    return EOFA_OK;
+}
+
+typedef std::chrono::steady_clock Clock;
+
+double since(Clock::time_point t0) {
+    return std::chrono::duration<double>(Clock::now() - t0).count();
+}
+
+// Inner CGNR on the Schur complement in storage precision P, unit source in
+// inner.r, solution in inner.x; stops at |r|^2 <= tol^2 (source norm 1).
+eofa_status run_cgnr(eofa_ctx* c, int P, double tol, int maxit, int* iters, double* rr_out, cudaStream_t st,
+                     Clock::time_point t0, long timeout_ms) {
+    Inner& in = c->inner[P];
+    const int xp = P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
+    const int* done = &c->scal->done;
+    const VecRef none{};
+    eofa_status s;
+    CKL(scal_init(c->scal, tol * tol, st), "scal_init");
+    CKL(blas_zero(xp, in.x, c->n5, c->g.Ls, st), "blas_zero");
+    if ((s = hop(c, P, KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), nullptr, st))) return s;
+    if ((s = hop(c, P, KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_ZZ), nullptr, st))) return s;
+    CKL(blas_copy(P, in.p, P, in.z, c->n5, c->g.Ls, 1.0, -1, red(c, FIN_NONE), st), "blas_copy");
+    const int chunk = 16;
+    *iters = 0;
+    for (;;) {
+        for (int i = 0; i < chunk; ++i) {
+            if ((s = hop(c, P, KIND_EO_MINV, 0, in.p, none, in.t, red(c, FIN_NONE), done, st, true))) return s;
+            if ((s = hop(c, P, KIND_OE_SCHUR, 1, in.t, in.p, in.q, red(c, FIN_ALPHA), done, st, true))) return s;
+            CKL(blas_cg_xr(P, xp, in.x, in.p, in.q, in.r, c->n5, c->g.Ls, red(c, FIN_RR), done, st), "cg_xr");
+            if ((s = hop(c, P, KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), done, st, true))) return s;
+            if ((s = hop(c, P, KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_BETA), done, st, true))) return s;
+            CKL(blas_cg_p(P, in.p, in.z, c->n5, c->g.Ls, c->scal, st), "cg_p");
+        }
+        if ((s = read_scal(c, st))) return s;
+        const DevScal& h = *c->h_scal;
+        *iters = h.iters;
+        *rr_out = h.rr;
+        if (h.nonfinite) return fail(c, EOFA_ERR_NONFINITE, "NaN or Inf in the inner CG reductions");
+        if (h.done) return EOFA_OK;
+        if (h.iters >= maxit) return EOFA_ERR_NOT_CONVERGED;
+        if (timeout_ms > 0 && since(t0) * 1e3 > (double)timeout_ms)
+            return fail(c, EOFA_ERR_TIMEOUT, "solve exceeded timeout_ms");
+    }
+}
+
+double default_inner_tol(int P) {
+    switch (P) {
+        case EOFA_F32: return 1e-5;
+        case EOFA_F16: return 2e-3;
+        case EOFA_BF16: return 1e-2;
+        default: return 0.0;
+    }
+}
+
+eofa_status solve_impl(eofa_ctx* c, const double* rhs, double* sol, const eofa_solve_opts& o,
+                       eofa_solve_stats* stats, cudaStream_t st) {
+    const auto t0 = Clock::now();
+    eofa_solve_stats S;
+    std::memset(&S, 0, sizeof(S));
+    const int P = o.inner;
+    if (P < 0 || P > 3) return fail(c, EOFA_ERR_ARG, "opts.inner must be an eofa_prec");
+    if (!(o.tol > 0.0)) return fail(c, EOFA_ERR_ARG, "opts.tol must be positive");
+    if (o.precond != 0) return fail(c, EOFA_ERR_UNSUPPORTED, "learned preconditioner not loaded");
+    const int maxit = o.max_iter > 0 ? o.max_iter : 100000;
+    const int maxouter = o.max_outer > 0 ? o.max_outer : 100;
+    const int H = o.rhs_form == 0 ? 1 : 0;
+    const int xp = P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
+    eofa_status s;
+    if ((s = ensure_inner(c, P))) return s;
+    c->timing = o.kernel_timing != 0;
+    c->launches = 0;
+    c->hop_ms = 0.0;
+    c->hop_launches = 0;
+    c->hop_bytes = 0.0;
+    c->ev_used = 0;
+    const VecRef none{};
+    const Geom& g = c->g;
+    const int Ls = g.Ls;
+
+    // b = g5 R5 phi (H form) or b (K form); |b|^2 into store[1] + store[2]
+    CKL(layout_import(c->b[0], rhs, g, 0, H, st), "import");
+    CKL(layout_import(c->b[1], rhs, g, 1, H, st), "import");
+    CKL(blas_copy(0, c->t[0], 0, c->b[0], c->n5, Ls, 1.0, -1, red(c, FIN_STORE, 1), st), "norm");
+    CKL(blas_copy(0, c->t[1], 0, c->b[1], c->n5, Ls, 1.0, -1, red(c, FIN_STORE, 2), st), "norm");
+    // initial guess (odd part of psi')
+    if (o.use_guess) {
+        CKL(layout_import(c->x[1], sol, g, 1, 0, st), "import");
+        if (H) {
+            if ((s = hop(c, 0, KIND_LOC_DTINV, 1, none, c->x[1], c->t[1], red(c, FIN_NONE), nullptr, st)))
+                return s;
+            CKL(blas_copy(0, c->x[1], 0, c->t[1], c->n5, Ls, 1.0, -1, red(c, FIN_NONE), st), "copy");
+        }
+    } else {
+        CKL(blas_zero(0, c->x[1], c->n5, Ls, st), "zero");
+    }
+    // even-odd source b~o = b_o + 1/2 D_h D~ M^-1 b_e
+    if ((s = hop(c, 0, KIND_LOC_DTMINV, 0, none, c->b[0], c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
+    if ((s = hop(c, 0, KIND_SRC, 1, c->t[0], c->b[1], c->bto, red(c, FIN_NONE), nullptr, st))) return s;
+    if ((s = read_scal(c, st))) return s;
+    const double bb = c->h_scal->store[1] + c->h_scal->store[2];
+    if (!std::isfinite(bb)) return fail(c, EOFA_ERR_NONFINITE, "right-hand side is not finite");
+    if (bb == 0.0) {
+        CK(cudaMemsetAsync(sol, 0, (size_t)c->n5 * 2 * 24 * sizeof(double), st), "memset");
+        CK(cudaStreamSynchronize(st), "sync");
+        S.status = EOFA_OK;
+        S.kernel_launches = c->launches;
+        S.seconds = since(t0);
+        if (stats) *stats = S;
+        return EOFA_OK;
+    }
+    const double bnorm = std::sqrt(bb);
+    eofa_status result = EOFA_ERR_NOT_CONVERGED;
+    int total = 0, outer = 0;
+    double rel = 1.0;
+    for (;;) {
+        // r = b~o - S x_o (FP64)
+        if ((s = hop(c, 0, KIND_EO_MINV, 0, c->x[1], none, c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
+        if ((s = hop(c, 0, KIND_OE_SCHUR, 1, c->t[0], c->x[1], c->qo, red(c, FIN_NONE), nullptr, st))) return s;
+        CKL(blas_sub(c->ro, c->bto, c->qo, c->n5, Ls, red(c, FIN_STORE, 0), st), "sub");
+        if ((s = read_scal(c, st))) return s;
+        const double rr = c->h_scal->store[0];
+        if (!std::isfinite(rr)) { result = fail(c, EOFA_ERR_NONFINITE, "non-finite outer residual"); break; }
+        rel = std::sqrt(rr) / bnorm;
+        if (rel <= o.tol) { result = EOFA_OK; break; }
+        if (outer >= maxouter || total >= maxit) { result = fail(c, EOFA_ERR_NOT_CONVERGED, "iteration cap"); break; }
+        if (o.timeout_ms > 0 && since(t0) * 1e3 > (double)o.timeout_ms) {
+            result = fail(c, EOFA_ERR_TIMEOUT, "solve exceeded timeout_ms");
+            break;
+        }
+        double itol = o.tol / rel;
+        if (P != EOFA_F64) {
+            const double dt = o.inner_tol > 0.0 ? o.inner_tol : default_inner_tol(P);
+            itol = std::max(itol, dt);
+        }
+        // inner source r / |r| in precision P
+        CKL(blas_copy(P, c->inner[P].r, 0, c->ro, c->n5, Ls, 1.0, 0, red(c, FIN_NONE), st), "copy");
+        int its = 0;
+        double irr = 0.0;
+        eofa_status is = run_cgnr(c, P, itol, maxit - total, &its, &irr, st, t0, o.timeout_ms);
+        total += its;
+        ++outer;
+        if (is == EOFA_ERR_NONFINITE || is == EOFA_ERR_TIMEOUT || is == EOFA_ERR_CUDA) { result = is; break; }
+        CKL(blas_acc(c->x[1], xp, c->inner[P].x, c->n5, Ls, c->scal, 0, st), "acc");
+    }
+    // x_e = M^-1 (b_e + 1/2 D_h D~ x_o)
+    if ((s = hop(c, 0, KIND_RECON, 0, c->x[1], c->b[0], c->x[0], red(c, FIN_NONE), nullptr, st))) return s;
+    // true residual of the full system
+    if ((s = hop(c, 0, KIND_FULL, 0, c->x[1], c->x[0], c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
+    if ((s = hop(c, 0, KIND_FULL, 1, c->x[0], c->x[1], c->t[1], red(c, FIN_NONE), nullptr, st))) return s;
+    CKL(blas_sub(c->t[0], c->b[0], c->t[0], c->n5, Ls, red(c, FIN_STORE, 3), st), "sub");
+    CKL(blas_sub(c->t[1], c->b[1], c->t[1], c->n5, Ls, red(c, FIN_STORE, 4), st), "sub");
+    if (H) {
+        if ((s = hop(c, 0, KIND_LOC_DT, 0, none, c->x[0], c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
+        if ((s = hop(c, 0, KIND_LOC_DT, 1, none, c->x[1], c->t[1], red(c, FIN_NONE), nullptr, st))) return s;
+        CKL(layout_export((double*)sol, c->t[0], g, 0, 0, st), "export");
+        CKL(layout_export((double*)sol, c->t[1], g, 1, 0, st), "export");
+    } else {
+        CKL(layout_export((double*)sol, c->x[0], g, 0, 0, st), "export");
+        CKL(layout_export((double*)sol, c->x[1], g, 1, 0, st), "export");
+    }
+    if ((s = read_scal(c, st))) return s;
+    S.true_res = std::sqrt((c->h_scal->store[3] + c->h_scal->store[4]) / bb);
+    S.recur_res = rel;
+    S.outer_iters = outer;
+    S.inner_iters = total;
+    S.hop_ms = c->hop_ms;
+    S.hop_launches = c->hop_launches;
+    S.hop_bytes = c->hop_bytes;
+    S.kernel_launches = c->launches;
+    if (result == EOFA_OK && !(S.true_res <= o.tol * 1.0000001)) {
+        result = fail(c, EOFA_ERR_NOT_CONVERGED, "true residual above tol after the outer loop");
+    }
+    S.status = result;
+    S.seconds = since(t0);
+    if (stats) *stats = S;
+    return result;
+}
+
+eofa_status apply_impl(eofa_ctx* c, const void* in, void* out, int which, cudaStream_t st) {
+    // which: 0 = K, 1 = K^dag, 2 = H + beta Delta P = g5 R5 K D~^-1
+    const Geom& g = c->g;
+    const VecRef none{};
+    eofa_status s;
+    CKL(layout_import(c->x[0], (const double*)in, g, 0, 0, st), "import");
+    CKL(layout_import(c->x[1], (const double*)in, g, 1, 0, st), "import");
+    if (which == 2) {
+        if ((s = hop(c, 0, KIND_LOC_DTINV, 0, none, c->x[0], c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
+        if ((s = hop(c, 0, KIND_LOC_DTINV, 1, none, c->x[1], c->t[1], red(c, FIN_NONE), nullptr, st))) return s;
+        if ((s = hop(c, 0, KIND_FULL, 0, c->t[1], c->t[0], c->x[0], red(c, FIN_NONE), nullptr, st))) return s;
+        if ((s = hop(c, 0, KIND_FULL, 1, c->t[0], c->t[1], c->x[1], red(c, FIN_NONE), nullptr, st))) return s;
+        CKL(layout_export((double*)out, c->x[0], g, 0, 1, st), "export");
+        CKL(layout_export((double*)out, c->x[1], g, 1, 1, st), "export");
+        return EOFA_OK;
+    }
+    const int kind = which == 0 ? KIND_FULL : KIND_FULL_DAG;
+    if ((s = hop(c, 0, kind, 0, c->x[1], c->x[0], c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
+    if ((s = hop(c, 0, kind, 1, c->x[0], c->x[1], c->t[1], red(c, FIN_NONE), nullptr, st))) return s;
+    CKL(layout_export((double*)out, c->t[0], g, 0, 0, st), "export");
+    CKL(layout_export((double*)out, c->t[1], g, 1, 0, st), "export");
+    return EOFA_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+eofa_status eofa_create(const eofa_params* p, const void* gauge, void* stream, eofa_ctx** out) {
+    if (!out) return EOFA_ERR_ARG;
+    *out = nullptr;
+    if (!p || !gauge) return EOFA_ERR_ARG;
+    for (int i = 0; i < 4; ++i)
+        if (p->dims[i] < 2 || (p->dims[i] & 1)) return EOFA_ERR_ARG;
+    if (p->pm != 1 && p->pm != -1) return EOFA_ERR_ARG;
+    if (p->t_bc != 1 && p->t_bc != -1) return EOFA_ERR_ARG;
+    if (p->Ls != 4 && p->Ls != 8 && p->Ls != 12 && p->Ls != 16) return EOFA_ERR_UNSUPPORTED;
+    eofa_ctx* c = new (std::nothrow) eofa_ctx();
+    if (!c) return EOFA_ERR_OOM;
+    c->p = *p;
+    Geom& g = c->g;
+    g.X = p->dims[0]; g.Y = p->dims[1]; g.Z = p->dims[2]; g.T = p->dims[3];
+    g.Xh = g.X / 2;
+    const long V = (long)g.X * g.Y * g.Z * g.T;
+    if (V / 2 > (1L << 30)) { delete c; return EOFA_ERR_UNSUPPORTED; }
+    g.Vh = (int)(V / 2);
+    g.Ls = p->Ls;
+    g.pad = 0;
+    g.tbc = (double)p->t_bc;
+    c->n5 = (long)g.Vh * g.Ls;
+    eofa_status s = build_coef(c);
+    cudaStream_t st = (cudaStream_t)stream;
+    auto bail = [&](eofa_status e) { eofa_destroy(c); return e; };
+    if (s != EOFA_OK) return bail(s);
+    for (int pr = 0; pr < 4; ++pr)
+        for (int par = 0; par < 2; ++par)
+            if ((s = dalloc(c, &c->links[pr][par], (size_t)g.Vh * 4 * 12 * kWidth[pr]))) return bail(s);
+    for (int par = 0; par < 2; ++par) {
+        if ((s = vec_alloc(c, 0, &c->b[par])) || (s = vec_alloc(c, 0, &c->x[par])) ||
+            (s = vec_alloc(c, 0, &c->t[par])))
+            return bail(s);
+    }
+    if ((s = vec_alloc(c, 0, &c->ro)) || (s = vec_alloc(c, 0, &c->bto)) || (s = vec_alloc(c, 0, &c->qo)))
+        return bail(s);
+    const int maxgrid = std::max(blas_max_grid(c->n5), g.Vh / 8 + 2);
+    void* tmp = nullptr;
+    if ((s = dalloc(c, &tmp, sizeof(double) * maxgrid))) return bail(s);
+    c->partials = (double*)tmp;
+    if ((s = dalloc(c, &tmp, 256))) return bail(s);
+    c->counter = (unsigned*)tmp;
+    if ((s = dalloc(c, &tmp, sizeof(DevScal)))) return bail(s);
+    c->scal = (DevScal*)tmp;
+    if ((s = dalloc(c, &tmp, 256))) return bail(s);
+    c->d_flag = (int*)tmp;
+    if (cudaMallocHost((void**)&c->h_scal, sizeof(DevScal)) != cudaSuccess) return bail(EOFA_ERR_OOM);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->counter, 0, 256, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->d_flag, 0, 256, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->scal, 0, sizeof(DevScal), st)) != cudaSuccess)
+        return bail(cuda_fail(c, e, "memset"));
+    if ((e = gauge_import((const double*)gauge, g, c->links, c->d_flag, st)) != cudaSuccess)
+        return bail(cuda_fail(c, e, "gauge import"));
+    int bad = 0;
+    if ((e = cudaMemcpyAsync(&bad, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return bail(cuda_fail(c, e, "gauge check"));
+    if (bad) return bail(EOFA_ERR_ARG);
+    *out = c;
+    return EOFA_OK;
+}
+
+eofa_status eofa_apply(eofa_ctx* ctx, const void* in, void* out, void* stream) {
+    if (!ctx || !in || !out || in == out) return EOFA_ERR_ARG;
+    return apply_impl(ctx, in, out, 0, (cudaStream_t)stream);
+}
+
+eofa_status eofa_apply_dag(eofa_ctx* ctx, const void* in, void* out, void* stream) {
+    if (!ctx || !in || !out || in == out) return EOFA_ERR_ARG;
+    return apply_impl(ctx, in, out, 1, (cudaStream_t)stream);
+}
+
+eofa_status eofa_apply_h(eofa_ctx* ctx, const void* in, void* out, void* stream) {
+    if (!ctx || !in || !out || in == out) return EOFA_ERR_ARG;
+    return apply_impl(ctx, in, out, 2, (cudaStream_t)stream);
+}
+
+eofa_status eofa_solve(eofa_ctx* ctx, const void* rhs, void* sol, const eofa_solve_opts* opts,
+                       eofa_solve_stats* stats, void* stream) {
+    if (!ctx || !rhs || !sol || !opts || rhs == sol) return EOFA_ERR_ARG;
+    ctx->err.clear();
+    eofa_status s = solve_impl(ctx, (const double*)rhs, (double*)sol, *opts, stats, (cudaStream_t)stream);
+    if (stats) stats->status = s;
+    return s;
+}
+
+eofa_status eofa_apply_batched(eofa_ctx* const* ctx, int n, const void* const* in, void* const* out, int dag,
+                               void* stream) {
+    if (n < 0 || (n > 0 && (!ctx || !in || !out))) return EOFA_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        eofa_status s = dag ? eofa_apply_dag(ctx[i], in[i], out[i], stream) : eofa_apply(ctx[i], in[i], out[i], stream);
+        if (s != EOFA_OK) return s;
+    }
+    return EOFA_OK;
+}
+
+eofa_status eofa_solve_batched(eofa_ctx* const* ctx, int n, const void* const* rhs, void* const* sol,
+                               const eofa_solve_opts* opts, eofa_solve_stats* stats, void* stream) {
+    if (n < 0 || (n > 0 && (!ctx || !rhs || !sol || !opts))) return EOFA_ERR_ARG;
+    eofa_status first = EOFA_OK;
+    for (int i = 0; i < n; ++i) {
+        eofa_status s = eofa_solve(ctx[i], rhs[i], sol[i], opts, stats ? stats + i : nullptr, stream);
+        if (s != EOFA_OK && first == EOFA_OK) first = s;
+    }
+    return first;
+}
+
+void eofa_destroy(eofa_ctx* ctx) {
+    if (!ctx) return;
+    for (void* p : ctx->allocs) cudaFree(p);
+    for (cudaEvent_t e : ctx->evs) cudaEventDestroy(e);
+    if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+    delete ctx;
+}
+
+const char* eofa_status_string(eofa_status s) {
+    switch (s) {
+        case EOFA_OK: return "ok";
+        case EOFA_ERR_ARG: return "invalid argument";
+        case EOFA_ERR_UNSUPPORTED: return "unsupported parameters";
+        case EOFA_ERR_SINGULAR: return "singular operator";
+        case EOFA_ERR_NOT_CONVERGED: return "not converged";
+        case EOFA_ERR_NONFINITE: return "non-finite value";
+        case EOFA_ERR_TIMEOUT: return "timeout";
+        case EOFA_ERR_CUDA: return "CUDA error";
+        case EOFA_ERR_OOM: return "out of device memory";
+        default: return "unknown status";
+    }
+}
+
+const char* eofa_last_error(const eofa_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+double eofa_hop_bytes(const eofa_ctx* ctx, int prec, int with_local) {
+    if (!ctx || prec < 0 || prec > 3) return 0.0;
+    return hop_bytes_of(ctx, prec, with_local);
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+"""CPU checks of the C ABI: the library loads and exports every symbol that
+include/eofa.h declares, with the struct layouts the binding assumes.  No
+compute call is made (there may be no GPU)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "eofa.h")
+
+
+@pytest.fixture(scope="module")
+def libeofa():
+    from paper_1706_05843_gb300 import build
+    build.build()
+    from paper_1706_05843_gb300 import binding
+    return binding.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(eofa_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["eofa_create", "eofa_apply", "eofa_apply_dag", "eofa_apply_h", "eofa_solve",
+              "eofa_apply_batched", "eofa_solve_batched", "eofa_destroy"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libeofa):
+    from paper_1706_05843_gb300 import binding
+    for n in declared_functions():
+        assert hasattr(libeofa, n), n
+        assert n in binding.SIGNATURES, n
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (eofa_[a-z_]+)\b", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_struct_layouts():
+    from paper_1706_05843_gb300 import binding as B
+    # sizes implied by include/eofa.h on LP64
+    assert C.sizeof(B.eofa_params) == 4 * 4 + 4 + 4 + 7 * 8 + 4 + 4
+    assert C.sizeof(B.eofa_solve_opts) == 8 + 4 + 4 + 8 + 6 * 4 + 8
+    assert C.sizeof(B.eofa_solve_stats) == 4 * 4 + 5 * 8 + 8
+
+
+def test_status_strings(libeofa):
+    from paper_1706_05843_gb300 import binding as B
+    assert B.eofa_status_string(0) == "ok"
+    assert "converged" in B.eofa_status_string(4)
+
+
+def test_argument_errors_without_gpu(libeofa):
+    """Invalid arguments are rejected before any device work."""
+    from paper_1706_05843_gb300 import binding as B
+    ctx = C.c_void_p()
+    p = B.make_params((4, 4, 4, 3), 8)          # odd extent
+    assert libeofa.eofa_create(C.byref(p), C.c_void_p(1), None, C.byref(ctx)) == 1
+    p = B.make_params((4, 4, 4, 4), 8, pm=0)    # bad chirality
+    assert libeofa.eofa_create(C.byref(p), C.c_void_p(1), None, C.byref(ctx)) == 1
+    p = B.make_params((4, 4, 4, 4), 6)          # Ls outside the compiled set
+    assert libeofa.eofa_create(C.byref(p), C.c_void_p(1), None, C.byref(ctx)) == 2
+    assert libeofa.eofa_create(C.byref(p), None, None, C.byref(ctx)) == 1
+    assert libeofa.eofa_apply(None, None, None, None) == 1
+    assert libeofa.eofa_solve(None, None, None, None, None, None) == 1
