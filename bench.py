@@ -200,6 +200,12 @@ def run_ours(args):
     sol = torch.empty_like(rhs)
     stream = torch.cuda.current_stream()
     opts = dict(tol=TOL, inner=args.inner)
+    if args.profile:
+        _, st = solver.solve(rhs, out=sol, max_iter=16, max_outer=1, check=False, kernel_timing=True, **opts)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": True, "inner_iters": st.inner_iters, "status": st.status}))
+        solver.close()
+        return
 
     def barrier():
         if ws > 1:
@@ -332,7 +338,11 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=8, help="oracle iterations per CPU sample")
     ap.add_argument("--quick", action="store_true", help="skip the other-precision solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--profile", action="store_true",
+                    help="one solve capped at 16 inner iterations, nothing else (for ncu captures)")
     args = ap.parse_args()
+    if args.profile:
+        args.quick, args.no_cpu, args.steps, args.warmup = True, True, 1, 0
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -130,6 +130,8 @@ def lib():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = None
+        L.oracle_apply_k_sites.argtypes = [P, vp, vp, vp, C.c_long, vp]
+        L.oracle_apply_k_sites.restype = None
         L.oracle_k.argtypes = [P, d, d]
         L.oracle_k.restype = d
         L.oracle_norm2.argtypes = [vp, C.c_long]
@@ -212,6 +214,14 @@ class Oracle:
     def k(self, x, dag=False):
         """Cayley-form K = D_DWF(m1) + pm beta u (x) v P_pm, or K^dag."""
         return self._op5(lib().oracle_apply_k, x, _ptr(self.U), dag=dag)
+
+    def k_sites(self, x, sites):
+        """(K x)(site, s) at the given lexicographic 4D sites, shape (n, Ls, 4, 3)."""
+        x = _c(x)
+        sites = np.ascontiguousarray(sites, dtype=np.int64)
+        out = np.empty((len(sites), self.a.Ls, 4, 3), dtype=np.complex128)
+        lib().oracle_apply_k_sites(C.byref(self.p), _ptr(self.U), _ptr(x), _ptr(sites), len(sites), _ptr(out))
+        return out
 
     # -- solves -------------------------------------------------------
     def _solve(self, fn, rhs, tol, maxit, guess):

@@ -652,6 +652,120 @@ void oracle_apply_k(const oracle_params *p, const cd *U, const cd *in, cd *out, 
     free(u);
 }
 
+/*
+ * (K psi)(x, s) for every s at the listed 4D sites only (lexicographic
+ * indices), written to out[i][s][spin][colour].  Same definitions as
+ * oracle_apply_k, evaluated site by site for lattices too large for the
+ * full-lattice oracle:  D_DWF psi = D_W chi + (psi - L psi) with
+ * chi = (c+d) psi + (c-d) L psi, which is Eq. (Ddwf) regrouped, and chi is
+ * site-local so D_W chi at x needs chi at x and its eight neighbours.
+ */
+static void chi_at(const oracle_params *p, const cd *psi, long xi, const double *Lp,
+                   const double *Lm, cd *chi)
+{
+    const int Ls = p->Ls;
+    const double cp = paper_c(p), d = paper_d(p);
+    for (int s = 0; s < Ls; ++s) {
+        cd acc[12];
+        for (int k = 0; k < 12; ++k) acc[k] = (cp + d) * psi[(xi * Ls + s) * 12 + k];
+        for (int t = 0; t < Ls; ++t) {
+            cd pp[12], pmv[12];
+            proj_chi(+1, psi + (xi * Ls + t) * 12, pp);
+            proj_chi(-1, psi + (xi * Ls + t) * 12, pmv);
+            for (int k = 0; k < 12; ++k)
+                acc[k] += (cp - d) * (Lp[s * Ls + t] * pp[k] + Lm[s * Ls + t] * pmv[k]);
+        }
+        for (int k = 0; k < 12; ++k) chi[s * 12 + k] = acc[k];
+    }
+}
+
+void oracle_apply_k_sites(const oracle_params *p, const cd *U, const cd *in,
+                          const long *sites, long nsites, cd *out)
+{
+    build_gammas();
+    const int Ls = p->Ls;
+    double *Lp = malloc(sizeof(double) * Ls * Ls);
+    double *Lm = malloc(sizeof(double) * Ls * Ls);
+    oracle_L_matrices(p, p->m1, Lp, Lm);
+    double *u = malloc(sizeof(double) * Ls);
+    double k;
+    oracle_uv(p, u, &k);
+    const double coef = p->pm * p->beta * k;
+    const int jstar = (p->pm > 0) ? Ls - 1 : 0;
+    const double diag = 4.0 - p->M5;
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < nsites; ++i) {
+        const long xi = sites[i];
+        int co[4];
+        site_coords(p, xi, co);
+        cd *chi = malloc(sizeof(cd) * Ls * 12);
+        cd *chn = malloc(sizeof(cd) * Ls * 12);
+        chi_at(p, in, xi, Lp, Lm, chi);
+        for (int s = 0; s < Ls; ++s) {
+            cd acc[12];
+            for (int q = 0; q < 12; ++q) acc[q] = diag * chi[s * 12 + q];
+            /* psi - L psi */
+            for (int t = 0; t < Ls; ++t) {
+                cd pp[12], pmv[12];
+                proj_chi(+1, in + (xi * Ls + t) * 12, pp);
+                proj_chi(-1, in + (xi * Ls + t) * 12, pmv);
+                for (int q = 0; q < 12; ++q)
+                    acc[q] += (s == t ? in[(xi * Ls + t) * 12 + q] : 0)
+                              - (Lp[s * Ls + t] * pp[q] + Lm[s * Ls + t] * pmv[q]);
+            }
+            for (int c = 0; c < 12; ++c) out[(i * Ls + s) * 12 + c] = acc[c];
+        }
+        for (int mu = 0; mu < 4; ++mu)
+            for (int dir = 0; dir < 2; ++dir) {
+                int cn[4] = {co[0], co[1], co[2], co[3]};
+                double phase = 1.0;
+                if (dir == 0) {
+                    cn[mu] = (co[mu] + 1) % p->dims[mu];
+                    if (mu == 3 && co[3] == p->dims[3] - 1) phase = p->t_bc;
+                } else {
+                    cn[mu] = (co[mu] - 1 + p->dims[mu]) % p->dims[mu];
+                    if (mu == 3 && co[3] == 0) phase = p->t_bc;
+                }
+                long ni = site_index(p, cn[0], cn[1], cn[2], cn[3]);
+                chi_at(p, in, ni, Lp, Lm, chn);
+                cd W[3][3];
+                if (dir == 0) {
+                    const cd *uu = U + (xi * 4 + mu) * 9;
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b) W[a][b] = uu[a * 3 + b];
+                } else {
+                    const cd *uu = U + (ni * 4 + mu) * 9;
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b) W[a][b] = conj(uu[b * 3 + a]);
+                }
+                double sg = (dir == 0) ? -1.0 : 1.0;
+                for (int s = 0; s < Ls; ++s) {
+                    cd t[12];
+                    for (int sp = 0; sp < 4; ++sp)
+                        for (int a = 0; a < 3; ++a) {
+                            cd sum = 0;
+                            for (int b = 0; b < 3; ++b) sum += W[a][b] * chn[s * 12 + sp * 3 + b];
+                            t[sp * 3 + a] = sum;
+                        }
+                    for (int sp = 0; sp < 4; ++sp)
+                        for (int a = 0; a < 3; ++a) {
+                            cd sum = t[sp * 3 + a];
+                            for (int sq = 0; sq < 4; ++sq) sum += sg * GAM[mu][sp][sq] * t[sq * 3 + a];
+                            out[(i * Ls + s) * 12 + sp * 3 + a] -= 0.5 * phase * sum;
+                        }
+                }
+            }
+        /* + pm beta k u_s P_pm psi_{j*} */
+        cd pj[12];
+        proj_chi(p->pm, in + (xi * Ls + jstar) * 12, pj);
+        for (int s = 0; s < Ls; ++s)
+            for (int q = 0; q < 12; ++q) out[(i * Ls + s) * 12 + q] += coef * u[s] * pj[q];
+        free(chi);
+        free(chn);
+    }
+    free(Lp); free(Lm); free(u);
+}
+
 /* ------------------------------------------------------------------ */
 /* vector helpers with a fixed summation order                         */
 /* ------------------------------------------------------------------ */

@@ -13,16 +13,44 @@ static inline int grid_for(long n) { return (int)((n + BT - 1) / BT); }
 // ---------------------------------------------------------------------------
 // scalars
 // ---------------------------------------------------------------------------
-__global__ void k_scal_init(DevScal* sc, double target_rr) {
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void k_scal_init(DevScal* sc, double target_rr, int max_iters, unsigned long long timeout_ns) {
     sc->qq = sc->zz = sc->rr = sc->alpha = sc->beta = 0.0;
     sc->target_rr = target_rr;
     sc->iters = 0;
     sc->done = 0;
     sc->nonfinite = 0;
+    sc->max_iters = max_iters;
+    sc->timeout_ns = timeout_ns;
+    sc->timed_out = 0;
+    sc->t0_ns = globaltimer_ns();
 }
 
-cudaError_t scal_init(DevScal* sc, double target_rr, cudaStream_t st) {
-    k_scal_init<<<1, 1, 0, st>>>(sc, target_rr);
+cudaError_t scal_init(DevScal* sc, double target_rr, int max_iters, unsigned long long timeout_ns,
+                      cudaStream_t st) {
+    k_scal_init<<<1, 1, 0, st>>>(sc, target_rr, max_iters, timeout_ns);
+    return cudaGetLastError();
+}
+
+// Condition of the device-driven CG loop (a WHILE node of a CUDA graph):
+// run the body again unless converged, non-finite, at the iteration cap or
+// past the deadline.  Every exit is bounded by max_iters.
+__global__ void k_while_cond(cudaGraphConditionalHandle h, DevScal* sc) {
+    int go = !sc->done && !sc->nonfinite && sc->iters < sc->max_iters;
+    if (go && sc->timeout_ns && globaltimer_ns() - sc->t0_ns > sc->timeout_ns) {
+        sc->timed_out = 1;
+        go = 0;
+    }
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+cudaError_t while_cond(cudaGraphConditionalHandle h, DevScal* sc, cudaStream_t st) {
+    k_while_cond<<<1, 1, 0, st>>>(h, sc);
     return cudaGetLastError();
 }
 

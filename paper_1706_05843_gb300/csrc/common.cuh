@@ -66,6 +66,10 @@ struct DevScal {
     int iters;
     int done;
     int nonfinite;
+    int max_iters;                 // device-driven loops stop here
+    unsigned long long t0_ns;      // %globaltimer at the start of the solve
+    unsigned long long timeout_ns; // 0: none
+    int timed_out;
     int pad;
 };
 

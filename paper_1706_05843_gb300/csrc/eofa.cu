@@ -57,6 +57,9 @@ struct eofa_ctx {
     double hop_bytes = 0.0;
     std::vector<double> ev_bytes;
     long launches = 0;  // kernels launched since the last reset
+    // device-driven CG loops, one per inner precision
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t cg_exec[4] = {};
 };
 
 namespace {
@@ -312,29 +315,116 @@ double since(Clock::time_point t0) {
 
 // Inner CGNR on the Schur complement in storage precision P, unit source in
 // inner.r, solution in inner.x; stops at |r|^2 <= tol^2 (source norm 1).
-eofa_status run_cgnr(eofa_ctx* c, int P, double tol, int maxit, int* iters, double* rr_out, cudaStream_t st,
-                     Clock::time_point t0, long timeout_ms) {
+// one CGNR iteration on the Schur complement (6 launches); every kernel
+// returns at once when the device flag scal->done is set
+eofa_status cg_iteration(eofa_ctx* c, int P, cudaStream_t st, bool timed) {
     Inner& in = c->inner[P];
     const int xp = P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
     const int* done = &c->scal->done;
     const VecRef none{};
     eofa_status s;
-    CKL(scal_init(c->scal, tol * tol, st), "scal_init");
+    if ((s = hop(c, P, KIND_EO_MINV, 0, in.p, none, in.t, red(c, FIN_NONE), done, st, timed))) return s;
+    if ((s = hop(c, P, KIND_OE_SCHUR, 1, in.t, in.p, in.q, red(c, FIN_ALPHA), done, st, timed))) return s;
+    CKL(blas_cg_xr(P, xp, in.x, in.p, in.q, in.r, c->n5, c->g.Ls, red(c, FIN_RR), done, st), "cg_xr");
+    if ((s = hop(c, P, KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), done, st, timed))) return s;
+    if ((s = hop(c, P, KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_BETA), done, st, timed))) return s;
+    CKL(blas_cg_p(P, in.p, in.z, c->n5, c->g.Ls, c->scal, st), "cg_p");
+    return EOFA_OK;
+}
+
+constexpr int kChunk = 16;  // iterations per graph body / per host check
+
+// Capture the CG loop of precision P once: a graph whose only node is a
+// conditional WHILE; its body holds kChunk iterations and the condition
+// kernel.  All pointers it bakes in belong to the context, so the graph is
+// replayed by every later solve.
+eofa_status build_cg_graph(eofa_ctx* c, int P) {
+    if (c->cg_exec[P]) return EOFA_OK;
+    if (!c->cap) CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0), "cudaGraphCreate");
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    // (the params union has no default constructor: zeroed raw storage)
+    alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+    std::memset(npbuf, 0, sizeof(npbuf));
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(npbuf);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(c, e, "conditional graph node");
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(c, e, "cudaStreamBeginCaptureToGraph");
+    }
+    const long launches0 = c->launches;
+    eofa_status s = EOFA_OK;
+    for (int i = 0; i < kChunk && s == EOFA_OK; ++i) s = cg_iteration(c, P, c->cap, false);
+    if (s == EOFA_OK) {
+        e = while_cond(h, c->scal, c->cap);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "while_cond");
+    }
+    cudaGraph_t captured = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->cap, &captured);
+    c->launches = launches0;
+    if (s == EOFA_OK && e2 != cudaSuccess) s = cuda_fail(c, e2, "cudaStreamEndCapture");
+    if (s == EOFA_OK) {
+        e = cudaGraphInstantiate(&c->cg_exec[P], g, 0);
+        if (e != cudaSuccess) {
+            c->cg_exec[P] = nullptr;
+            s = cuda_fail(c, e, "cudaGraphInstantiate");
+        }
+    }
+    cudaGraphDestroy(g);
+    return s;
+}
+
+// Inner CGNR on the Schur complement in storage precision P, unit source in
+// inner.r, solution in inner.x; stops at |r|^2 <= tol^2 (source norm 1).
+// Without kernel timing the loop runs on the device (one graph launch, no
+// host round trip); with timing it is driven from the host, with CUDA events
+// around every hop kernel.
+eofa_status run_cgnr(eofa_ctx* c, int P, double tol, int maxit, int* iters, double* rr_out, cudaStream_t st,
+                     Clock::time_point t0, long timeout_ms) {
+    Inner& in = c->inner[P];
+    const int xp = P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
+    const VecRef none{};
+    eofa_status s;
+    double left_ms = 0.0;
+    if (timeout_ms > 0) {
+        left_ms = (double)timeout_ms - since(t0) * 1e3;
+        if (left_ms <= 0.0) return fail(c, EOFA_ERR_TIMEOUT, "solve exceeded timeout_ms");
+    }
+    CKL(scal_init(c->scal, tol * tol, maxit, (unsigned long long)(left_ms * 1e6), st), "scal_init");
     CKL(blas_zero(xp, in.x, c->n5, c->g.Ls, st), "blas_zero");
     if ((s = hop(c, P, KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), nullptr, st))) return s;
     if ((s = hop(c, P, KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_ZZ), nullptr, st))) return s;
     CKL(blas_copy(P, in.p, P, in.z, c->n5, c->g.Ls, 1.0, -1, red(c, FIN_NONE), st), "blas_copy");
-    const int chunk = 16;
     *iters = 0;
+    if (!c->timing) {
+        if ((s = build_cg_graph(c, P))) return s;
+        CK(cudaGraphLaunch(c->cg_exec[P], st), "cudaGraphLaunch");
+        if ((s = read_scal(c, st))) return s;
+        const DevScal& h = *c->h_scal;
+        *iters = h.iters;
+        *rr_out = h.rr;
+        c->launches += (long)(6 * kChunk + 1) * ((h.iters + kChunk - 1) / kChunk + (h.iters == 0 ? 1 : 0));
+        if (h.nonfinite) return fail(c, EOFA_ERR_NONFINITE, "NaN or Inf in the inner CG reductions");
+        if (h.done) return EOFA_OK;
+        if (h.timed_out) return fail(c, EOFA_ERR_TIMEOUT, "solve exceeded timeout_ms");
+        return EOFA_ERR_NOT_CONVERGED;
+    }
     for (;;) {
-        for (int i = 0; i < chunk; ++i) {
-            if ((s = hop(c, P, KIND_EO_MINV, 0, in.p, none, in.t, red(c, FIN_NONE), done, st, true))) return s;
-            if ((s = hop(c, P, KIND_OE_SCHUR, 1, in.t, in.p, in.q, red(c, FIN_ALPHA), done, st, true))) return s;
-            CKL(blas_cg_xr(P, xp, in.x, in.p, in.q, in.r, c->n5, c->g.Ls, red(c, FIN_RR), done, st), "cg_xr");
-            if ((s = hop(c, P, KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), done, st, true))) return s;
-            if ((s = hop(c, P, KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_BETA), done, st, true))) return s;
-            CKL(blas_cg_p(P, in.p, in.z, c->n5, c->g.Ls, c->scal, st), "cg_p");
-        }
+        for (int i = 0; i < kChunk; ++i)
+            if ((s = cg_iteration(c, P, st, true))) return s;
         if ((s = read_scal(c, st))) return s;
         const DevScal& h = *c->h_scal;
         *iters = h.iters;
@@ -623,6 +713,9 @@ void eofa_destroy(eofa_ctx* ctx) {
     if (!ctx) return;
     for (void* p : ctx->allocs) cudaFree(p);
     for (cudaEvent_t e : ctx->evs) cudaEventDestroy(e);
+    for (int i = 0; i < 4; ++i)
+        if (ctx->cg_exec[i]) cudaGraphExecDestroy(ctx->cg_exec[i]);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
     delete ctx;
 }

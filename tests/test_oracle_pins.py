@@ -431,3 +431,15 @@ def test_solve_free_field_closed_form(oracle_mod):
     psip, st = o.solve_k(b, tol=1e-13)
     assert st.converged
     assert rel(psip, phase[..., None, None, None] * sol) < 1e-10
+
+
+@pytest.mark.parametrize("coef", [MOBIUS, SHAMIR])
+@pytest.mark.parametrize("pm", [1, -1])
+def test_k_at_sites_matches_full_lattice(oracle_mod, coef, pm):
+    """The site-by-site evaluation (used at full benchmark sizes) agrees with
+    the full-lattice operator: Eq. (Ddwf) regrouped as D_W chi + psi - L psi."""
+    o = make(oracle_mod, dims=(4, 4, 2, 6), Ls=8, pm=pm, beta=0.7, m3=0.3, **coef)
+    psi = I.gaussian_fermion(o.a.dims, 8, 51)
+    full = o.k(psi).reshape(-1, 8, 4, 3)
+    sites = np.array([0, 1, 5, 17, 63, 100, 191])
+    assert rel(o.k_sites(psi, sites), full[sites]) < 1e-14
