@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(BT) k_cg_xr(VecRef x, VecRef p, VecRef q, VecR
     typedef typename Traits<SX>::R RX;
     if (*done) return;
     const long t = (long)blockIdx.x * BT + threadIdx.x;
-    double nn = 0.0;
+    R nn = (R)0;
     if (t < n5) {
         const long xcb = t / Ls;
         const int s = (int)(t - xcb * Ls);
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(BT) k_cg_xr(VecRef x, VecRef p, VecRef q, VecR
         for (int i = 0; i < 24; ++i) {
             xv[i] += (RX)al * (RX)pv[i];
             rv[i] -= (R)al * qv[i];
-            nn += (double)rv[i] * (double)rv[i];
+            nn += rv[i] * rv[i];
         }
         store_sp<SX, RX>(x.d, x.n, xcb, s, Ls, xv);
         store_sp<S, R>(r.d, r.n, xcb, s, Ls, rv);
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(BT) k_copy(VecRef dst, VecRef src, long n5, in
     typedef typename Traits<SD>::R RD;
     typedef typename Traits<SS>::R RS;
     const long t = (long)blockIdx.x * BT + threadIdx.x;
-    double nn = 0.0;
+    RD nn = (RD)0;
     if (t < n5) {
         const long xcb = t / Ls;
         const int s = (int)(t - xcb * Ls);
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(BT) k_copy(VecRef dst, VecRef src, long n5, in
 #pragma unroll
         for (int i = 0; i < 24; ++i) {
             dv[i] = (RD)((double)sv[i] * a);
-            nn += (double)dv[i] * (double)dv[i];
+            nn += dv[i] * dv[i];
         }
         store_sp<SD, RD>(dst.d, dst.n, xcb, s, Ls, dv);
     }

@@ -345,14 +345,17 @@ __device__ __forceinline__ void finalize(const Reduce& rd, double total) {
     }
 }
 
-template <int NT>
-__device__ __forceinline__ void block_reduce_finalize(double v, const Reduce& rd) {
+// The per-thread value and the warp-level sum are kept in the kernel's
+// compute precision R (FP32 kernels must not touch GB300's slow FP64 pipe
+// per element); warp sums are combined in FP64.
+template <int NT, typename R>
+__device__ __forceinline__ void block_reduce_finalize(R v, const Reduce& rd) {
     __shared__ double red_ws[NT / 32];
     __shared__ int red_last;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) red_ws[w] = v;
+    if (l == 0) red_ws[w] = (double)v;
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;

@@ -117,23 +117,27 @@ __device__ __forceinline__ void hop_dir(R* __restrict__ acc, const R* __restrict
     for (int sp = 0; sp < 2; ++sp) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            C2<R> sum = {0, 0};
+            // complex multiply-accumulate as plain FMA chains (4 per term)
+            R re = (R)0, im = (R)0;
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
-                C2<R> hb = {h[sp * 6 + 2 * b], h[sp * 6 + 2 * b + 1]};
-                C2<R> t;
-                if constexpr (!ADJ) {
-                    C2<R> ua = {u[(a * 3 + b) * 2], u[(a * 3 + b) * 2 + 1]};
-                    t = cmul(ua, hb);
-                } else {
-                    C2<R> ub = {u[(b * 3 + a) * 2], u[(b * 3 + a) * 2 + 1]};
-                    t = cmulc(ub, hb);
+                const R hr = h[sp * 6 + 2 * b], hi = h[sp * 6 + 2 * b + 1];
+                if constexpr (!ADJ) {       // U_ab h_b
+                    const R ur = u[(a * 3 + b) * 2], ui = u[(a * 3 + b) * 2 + 1];
+                    if (b == 0) { re = ur * hr; im = ur * hi; }
+                    else { re = fma(ur, hr, re); im = fma(ur, hi, im); }
+                    re = fma(-ui, hi, re);
+                    im = fma(ui, hr, im);
+                } else {                    // conj(U_ba) h_b
+                    const R ur = u[(b * 3 + a) * 2], ui = u[(b * 3 + a) * 2 + 1];
+                    if (b == 0) { re = ur * hr; im = ur * hi; }
+                    else { re = fma(ur, hr, re); im = fma(ur, hi, im); }
+                    re = fma(ui, hi, re);
+                    im = fma(-ui, hr, im);
                 }
-                sum.re += t.re;
-                sum.im += t.im;
             }
-            w[sp * 6 + 2 * a] = sum.re * phase;
-            w[sp * 6 + 2 * a + 1] = sum.im * phase;
+            w[sp * 6 + 2 * a] = re * phase;
+            w[sp * 6 + 2 * a + 1] = im * phase;
         }
     }
     // reconstruct: upper += w, lower += SG B^dag w
@@ -308,6 +312,11 @@ template <typename R> struct ShStride;
 template <> struct ShStride<float> { static constexpr int V = 28; };   // 112 B rows: conflict-free float4
 template <> struct ShStride<double> { static constexpr int V = 26; };  // 208 B rows: conflict-free double2
 
+// one staged link: 18 reals padded to a multiple of 16 bytes
+template <typename R> struct LinkStride;
+template <> struct LinkStride<float> { static constexpr int V = 20; };
+template <> struct LinkStride<double> { static constexpr int V = 18; };
+
 template <int LS> struct Tile {
     static constexpr int NS = (LS >= 16) ? 8 : (LS == 12 ? 16 : 128 / LS);
     static constexpr int NT = NS * LS;
@@ -335,18 +344,51 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
     const bool valid = xcb < a.g.Vh;
     const int row = il * LS + s;
 
+    // ---------------- phase 0: links and neighbours, once per 4D site ---
+    // The 8 links of each site (4 forward from this parity, 4 backward from
+    // the neighbours) are loaded once, their third row rebuilt, and kept in
+    // shared memory for all Ls slices of the site, together with the 8
+    // neighbour indices (bit 31: the hop crosses the time boundary).
+    R* sl = sy + (KT::HASY ? NS * LS * ST : 0);   // [NS][8][LK]
+    constexpr int LK = LinkStride<R>::V;
+    unsigned* snb = reinterpret_cast<unsigned*>(sl + NS * 8 * LK);  // [NS][8]
+    if constexpr (KT::HOP) {
+        const Geom& g = a.g;
+        for (int j = tid; j < NS * 8; j += NT) {
+            const int jl = j >> 3, d = j & 7, mu = d & 3;
+            const long jcb = (long)blockIdx.x * NS + jl;
+            if (jcb < g.Vh) {
+                int rem = (int)jcb;
+                const int xh = rem % g.Xh; rem /= g.Xh;
+                const int y = rem % g.Y; rem /= g.Y;
+                const int z = rem % g.Z;
+                const int t = rem / g.Z;
+                int cn[4] = {2 * xh + ((a.out_par + y + z + t) & 1), y, z, t};
+                const int dm[4] = {g.X, g.Y, g.Z, g.T};
+                unsigned edge = 0u;
+                if (d < 4) {
+                    edge = (mu == 3 && cn[3] == dm[3] - 1) ? 0x80000000u : 0u;
+                    cn[mu] = (cn[mu] + 1 == dm[mu]) ? 0 : cn[mu] + 1;
+                } else {
+                    edge = (mu == 3 && cn[3] == 0) ? 0x80000000u : 0u;
+                    cn[mu] = (cn[mu] == 0) ? dm[mu] - 1 : cn[mu] - 1;
+                }
+                const long ncb = ((((long)cn[3] * g.Z + cn[2]) * g.Y + cn[1]) * g.X + cn[0]) >> 1;
+                snb[j] = (unsigned)ncb | edge;
+                R u[18];
+                if (d < 4) load_link<S, R>(a.lk_out, jcb, mu, u);
+                else load_link<S, R>(a.lk_in, ncb, mu, u);
+                rebuild_row2(u);
+#pragma unroll
+                for (int i = 0; i < 18; ++i) sl[j * LK + i] = u[i];
+            }
+        }
+        __syncthreads();
+    }
+
     // ---------------- phase 1: hop and staging --------------------------
     if (valid) {
         if constexpr (KT::HOP) {
-            const Geom& g = a.g;
-            int rem = (int)xcb;
-            const int xh = rem % g.Xh; rem /= g.Xh;
-            const int y = rem % g.Y; rem /= g.Y;
-            const int z = rem % g.Z;
-            const int t = rem / g.Z;
-            const int x = 2 * xh + ((a.out_par + y + z + t) & 1);
-            const int co[4] = {x, y, z, t};
-            const int dm[4] = {g.X, g.Y, g.Z, g.T};
             R acc[24];
 #pragma unroll
             for (int i = 0; i < 24; ++i) acc[i] = (R)0;
@@ -355,16 +397,9 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
             for (int mu = 0; mu < 4; ++mu) {
 #pragma unroll
                 for (int dir = 0; dir < 2; ++dir) {
-                    int cn[4] = {co[0], co[1], co[2], co[3]};
-                    R ph = (R)1;
-                    if (dir == 0) {
-                        cn[mu] = (co[mu] + 1 == dm[mu]) ? 0 : co[mu] + 1;
-                        if (mu == 3 && co[3] == dm[3] - 1) ph = (R)g.tbc;
-                    } else {
-                        cn[mu] = (co[mu] == 0) ? dm[mu] - 1 : co[mu] - 1;
-                        if (mu == 3 && co[3] == 0) ph = (R)g.tbc;
-                    }
-                    const long ncb = ((((long)cn[3] * g.Z + cn[2]) * g.Y + cn[1]) * g.X + cn[0]) >> 1;
+                    const unsigned nb = snb[il * 8 + dir * 4 + mu];
+                    const long ncb = (long)(nb & 0x7fffffffu);
+                    const R ph = (mu == 3 && (nb >> 31)) ? (R)a.g.tbc : (R)1;
                     R p[24];
                     load_sp<S, R>(a.in, a.in_nrm, ncb, s, LS, p);
                     if constexpr (KT::PRE) {
@@ -382,9 +417,11 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
                         for (int i = 0; i < 12; ++i) p[12 + i] += fd * q[i];
                     }
                     R u[18];
-                    if (dir == 0) load_link<S, R>(a.lk_out, xcb, mu, u);
-                    else load_link<S, R>(a.lk_in, ncb, mu, u);
-                    rebuild_row2(u);
+                    {
+                        const R* src = sl + (il * 8 + dir * 4 + mu) * LK;
+#pragma unroll
+                        for (int i = 0; i < 18; ++i) u[i] = src[i];
+                    }
                     if (dir == 0) {
                         if (mu == 0) hop_dir<R, 0, FS, false>(acc, p, u, ph);
                         if (mu == 1) hop_dir<R, 1, FS, false>(acc, p, u, ph);
@@ -483,7 +520,7 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
     __syncthreads();
 
     // ---------------- phase 3: store + reduction ------------------------
-    double nn = 0.0;
+    R nn = (R)0;
     if (valid) {
         R v[24];
 #pragma unroll
@@ -491,16 +528,17 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
         store_sp<S, R>(a.out, a.out_nrm, xcb, s, LS, v);
         if (a.rd.fin != FIN_NONE) {
 #pragma unroll
-            for (int i = 0; i < 24; ++i) nn += (double)v[i] * (double)v[i];
+            for (int i = 0; i < 24; ++i) nn += v[i] * v[i];
         }
     }
     if (a.rd.fin != FIN_NONE) block_reduce_finalize<NT>(nn, a.rd);
 }
 
-template <typename S, int LS>
+template <typename S, int LS, int K>
 constexpr size_t hop_smem_bytes() {
     typedef typename Traits<S>::R R;
-    return 2ull * Tile<LS>::NT * ShStride<R>::V * sizeof(R);
+    return ((1 + (KindTraits<K>::HASY ? 1 : 0)) * (size_t)Tile<LS>::NT * ShStride<R>::V +
+            (KindTraits<K>::HOP ? (size_t)Tile<LS>::NS * 8 * (LinkStride<R>::V + 1) : 0)) * sizeof(R);
 }
 
 }  // namespace eofa

@@ -13,7 +13,7 @@ static cudaError_t launch_one(const HopArgs& a, const SCoef<typename Traits<S>::
     typedef typename Traits<S>::R R;
     constexpr int NT = Tile<LS>::NT;
     constexpr int NS = Tile<LS>::NS;
-    const size_t smem = (1 + (KindTraits<K>::HASY ? 1 : 0)) * (size_t)NT * ShStride<R>::V * sizeof(R);
+    const size_t smem = hop_smem_bytes<S, LS, K>();
     static bool attr_done = false;  // per instantiation; set before first launch
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(hop_kernel<S, LS, K>,
