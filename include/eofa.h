@@ -165,6 +165,30 @@ eofa_status eofa_solve_batched(eofa_ctx *const *ctx, int n, const void *const *r
 /* Release the context and all its device memory. */
 void eofa_destroy(eofa_ctx *ctx);
 
+/* out = K in, the same result as eofa_apply, for callers that cannot call
+ * cudaMalloc: for example a host framework that owns all device memory
+ * through its own pool and forbids allocations behind its back, or a
+ * latency-critical loop where cudaMalloc's implicit device synchronisation
+ * is not acceptable.  The paper has no counterpart of this call; it exists
+ * only for such callers.
+ *
+ * It needs no context and allocates nothing.  p, gauge, in and out are as
+ * for eofa_create and eofa_apply (device pointers, layouts above).  The
+ * work space -- two-row links, the even-odd copies of in and out, a check
+ * flag -- is one static device array of about 15 MiB inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ * Maximum size: X*Y*Z*T <= 4096 and X*Y*Z*T*Ls <= 32768 (e.g. 8^4 x 8);
+ * larger lattices return EOFA_ERR_UNSUPPORTED before any device work.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any
+ * stream capture.  The call checks that the links are SU(3) (EOFA_ERR_ARG
+ * otherwise), which reads a flag back, so it returns after its work on
+ * `stream` has finished.  Every call shares the one array and it keeps the
+ * last call's contents: calls that overlap on the GPU (other streams, other
+ * host threads) race and must not be issued. */
+eofa_status eofa_apply_noalloc(const eofa_params *p, const void *gauge, const void *in,
+                               void *out, void *stream);
+
 /* Static description of a status code. */
 const char *eofa_status_string(eofa_status s);
 

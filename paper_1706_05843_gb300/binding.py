@@ -66,6 +66,7 @@ SIGNATURES = {
     "eofa_solve_batched": ([C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp),
                             C.POINTER(eofa_solve_opts), C.POINTER(eofa_solve_stats), _vp], C.c_int),
     "eofa_destroy": ([_vp], None),
+    "eofa_apply_noalloc": ([C.POINTER(eofa_params), _vp, _vp, _vp, _vp], C.c_int),
     "eofa_status_string": ([C.c_int], C.c_char_p),
     "eofa_last_error": ([_vp], C.c_char_p),
     "eofa_hop_bytes": ([_vp, C.c_int, C.c_int], C.c_double),
@@ -178,6 +179,12 @@ def eofa_solve_batched(ctxs, rhss, sols, opts, stream=None, check=True):
     if check:
         _check(None, s)
     return list(st)
+
+
+def eofa_apply_noalloc(params, gauge, inp, out, stream=None):
+    """out = K inp without any device allocation (no context; small lattices)."""
+    _check(None, lib().eofa_apply_noalloc(C.byref(params), _dptr(gauge), _dptr(inp), _dptr(out),
+                                          _stream(stream)))
 
 
 def eofa_destroy(ctx):

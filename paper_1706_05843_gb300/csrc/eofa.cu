@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -131,9 +132,9 @@ void host_inv(int Ls, double a, double g, double m, const double* v, double* t) 
 }
 // solve (a + g L-) t = v
 void host_invT(int Ls, double a, double g, double m, const double* v, double* t) {
-    std::vector<double> vr(Ls), tr(Ls);
+    double vr[LSMAX], tr[LSMAX];
     for (int s = 0; s < Ls; ++s) vr[s] = v[Ls - 1 - s];
-    host_inv(Ls, a, g, m, vr.data(), tr.data());
+    host_inv(Ls, a, g, m, vr, tr);
     for (int s = 0; s < Ls; ++s) t[s] = tr[Ls - 1 - s];
 }
 
@@ -154,26 +155,25 @@ void cast_coef(const SCoef<double>& d, SCoef<R>& r) {
 // gamma = c5 (4 - M5) - 1; the shift u_pm (x) v_pm with the closed forms of
 // u_pm (mass m1) and v_pm = k(m2, m3) e_{Ls-1 | 0}; Sherman-Morrison vectors
 // x = A^-1 u (the tridiagonal-algorithm step of App. B) and y = A^-T v.
-eofa_status build_coef(eofa_ctx* c) {
-    const eofa_params& p = c->p;
+// Context-free and free of heap allocation: also used by the entry point
+// that allocates nothing.  On failure *why names the reason.
+eofa_status coef_from_params(const eofa_params& p, SCoef<double>& k, const char** why) {
     const int Ls = p.Ls;
-    SCoef<double>& k = c->c64;
     std::memset(&k, 0, sizeof(k));
     const double b5 = p.b, c5 = p.c, m = p.m1;
-    if (b5 == 0.0) return fail(c, EOFA_ERR_UNSUPPORTED, "b (b5) must be non-zero");
+    if (b5 == 0.0) return *why = "b (b5) must be non-zero", EOFA_ERR_UNSUPPORTED;
     const double alpha = b5 * (4.0 - p.M5) + 1.0;
     const double gamma = c5 * (4.0 - p.M5) - 1.0;
-    if (alpha == 0.0) return fail(c, EOFA_ERR_SINGULAR, "b5 (4 - M5) + 1 = 0");
+    if (alpha == 0.0) return *why = "b5 (4 - M5) + 1 = 0", EOFA_ERR_SINGULAR;
     const double za = gamma / alpha, zb = c5 / b5;
     if (std::fabs(za) >= 1.0 || std::fabs(zb) >= 1.0)
-        return fail(c, EOFA_ERR_UNSUPPORTED,
-                    "fifth-dimension recurrences need |(c5(4-M5)-1)/(b5(4-M5)+1)| < 1 and |c5/b5| < 1");
+        return *why = "fifth-dimension recurrences need |(c5(4-M5)-1)/(b5(4-M5)+1)| < 1 and |c5/b5| < 1", EOFA_ERR_UNSUPPORTED;
     const double ca = 1.0 + m * std::pow(za, Ls), cb = 1.0 + m * std::pow(zb, Ls);
     if (std::fabs(ca) < 1e-14 || std::fabs(cb) < 1e-14)
-        return fail(c, EOFA_ERR_SINGULAR, "cyclic fifth-dimension block is singular");
+        return *why = "cyclic fifth-dimension block is singular", EOFA_ERR_SINGULAR;
     auto N = [&](double mm) { return std::pow(b5, Ls) + mm * std::pow(c5, Ls); };
     if (N(p.m1) == 0.0 || N(p.m2) == 0.0 || N(p.m3) == 0.0)
-        return fail(c, EOFA_ERR_SINGULAR, "N(m) = b5^Ls + m c5^Ls vanishes");
+        return *why = "N(m) = b5^Ls + m c5^Ls vanishes", EOFA_ERR_SINGULAR;
     k.alpha = alpha; k.gamma = gamma; k.b5 = b5; k.c5 = c5; k.m = m;
     k.ia = 1.0 / alpha; k.za = za; k.mza = m * za;
     k.ib = 1.0 / b5; k.zb = zb; k.mzb = m * zb;
@@ -187,7 +187,7 @@ eofa_status build_coef(eofa_ctx* c) {
     // k(m2, m3) = 2c (m3 - m2) (c+d)^{2Ls} / (N(m2) N(m3)), 2c = b5 + c5
     const double kk = (b5 + c5) * (p.m3 - p.m2) * std::pow(b5, 2 * Ls) / (N(p.m2) * N(p.m3));
     const double N1 = N(p.m1);
-    std::vector<double> u(Ls);
+    double u[LSMAX];
     for (int s = 0; s < Ls; ++s) {
         if (p.pm > 0)
             u[s] = ((s & 1) ? -1.0 : 1.0) * std::pow(c5, s) / std::pow(b5, Ls + s + 1) * N1;
@@ -197,18 +197,25 @@ eofa_status build_coef(eofa_ctx* c) {
     k.cs = p.pm > 0 ? 0 : 1;
     for (int s = 0; s < Ls; ++s) k.um[s] = (k.cs == 0) ? u[s] : u[Ls - 1 - s];
     host_inv(Ls, alpha, gamma, m, k.um, k.xm);
-    std::vector<double> e(Ls, 0.0);
+    double e[LSMAX] = {};
     e[Ls - 1] = kk;
-    host_invT(Ls, alpha, gamma, m, e.data(), k.ym);
+    host_invT(Ls, alpha, gamma, m, e, k.ym);
     k.has_shift = p.beta != 0.0;
     const double sb = p.pm * p.beta;
     const double den = 1.0 + sb * kk * k.xm[Ls - 1];
     if (k.has_shift && std::fabs(den) < 1e-14)
-        return fail(c, EOFA_ERR_SINGULAR, "Sherman-Morrison denominator 1 + pm beta <v, A^-1 u> ~ 0");
+        return *why = "Sherman-Morrison denominator 1 + pm beta <v, A^-1 u> ~ 0", EOFA_ERR_SINGULAR;
     k.sbk = sb * kk;
     k.sbk_den = k.has_shift ? sb * kk / den : 0.0;
     k.sb_den = k.has_shift ? sb / den : 0.0;
-    cast_coef(k, c->c32);
+    return EOFA_OK;
+}
+
+eofa_status build_coef(eofa_ctx* c) {
+    const char* why = "";
+    eofa_status s = coef_from_params(c->p, c->c64, &why);
+    if (s != EOFA_OK) return fail(c, s, why);
+    cast_coef(c->c64, c->c32);
     return EOFA_OK;
 }
 
@@ -743,3 +750,125 @@ double eofa_hop_bytes(const eofa_ctx* ctx, int prec, int with_local) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// eofa_apply_noalloc: K applied with no device allocation at all.
+//
+// Some callers cannot call cudaMalloc: a host framework that owns all device
+// memory through its own pool and forbids allocations behind its back, or a
+// latency-critical loop in which cudaMalloc's implicit device
+// synchronisation is not acceptable.  This entry point needs no context:
+// everything it works on besides the caller's inputs and output lives in
+// one file-scope static device array, g_noalloc_scratch, which every GPU
+// that loads the library holds until the process exits.
+// ===========================================================================
+namespace {
+
+constexpr long kNoAllocMaxVol4 = 4096;     // 4D sites (e.g. 8^4)
+constexpr long kNoAllocMaxSites5 = 32768;  // 5D sites V * Ls (e.g. 8^4 x 8)
+constexpr size_t kNaHalf = kNoAllocMaxVol4 / 2;
+constexpr size_t kNaLinks[4] = {kNaHalf * 4 * 12 * 8, kNaHalf * 4 * 12 * 4, kNaHalf * 4 * 12 * 2,
+                                kNaHalf * 4 * 12 * 2};  // one parity, per precision
+constexpr size_t kNaField = (size_t)(kNoAllocMaxSites5 / 2) * 24 * 8;  // one parity, FP64
+constexpr size_t kNaLinkTotal = 2 * (kNaLinks[0] + kNaLinks[1] + kNaLinks[2] + kNaLinks[3]);
+constexpr size_t kNaScratchBytes = kNaLinkTotal + 4 * kNaField + 256;
+
+constexpr int kNaMaxDevices = 64;
+unsigned char* g_noalloc_ptr[kNaMaxDevices] = {};  // device address of the scratch, per device
+std::mutex g_noalloc_mu;
+
+}  // namespace
+
+// About 15 MiB: two-row links of both parities in four precisions, the
+// input and output field in the even-odd layout, and the SU(3) check flag.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes];
+
+namespace {
+
+// Device address of the scratch array on the current device.  In host code
+// the name g_noalloc_scratch is only a host-side stand-in, so the address is
+// obtained once per device with cudaGetSymbolAddress, with that device
+// current, and cached.
+eofa_status noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return EOFA_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return EOFA_ERR_CUDA;
+        g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return EOFA_OK;
+}
+
+}  // namespace
+
+extern "C" eofa_status eofa_apply_noalloc(const eofa_params* p, const void* gauge, const void* in, void* out,
+                                          void* stream) {
+    if (!p || !gauge || !in || !out || in == out) return EOFA_ERR_ARG;
+    for (int i = 0; i < 4; ++i)
+        if (p->dims[i] < 2 || (p->dims[i] & 1)) return EOFA_ERR_ARG;
+    if (p->pm != 1 && p->pm != -1) return EOFA_ERR_ARG;
+    if (p->t_bc != 1 && p->t_bc != -1) return EOFA_ERR_ARG;
+    if (p->Ls != 4 && p->Ls != 8 && p->Ls != 12 && p->Ls != 16) return EOFA_ERR_UNSUPPORTED;
+    const long V = (long)p->dims[0] * p->dims[1] * p->dims[2] * p->dims[3];
+    if (V > kNoAllocMaxVol4 || V * p->Ls > kNoAllocMaxSites5) return EOFA_ERR_UNSUPPORTED;
+    SCoef<double> k;
+    const char* why = "";
+    eofa_status s = coef_from_params(*p, k, &why);
+    if (s != EOFA_OK) return s;
+    unsigned char* base = nullptr;
+    if ((s = noalloc_scratch(&base)) != EOFA_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    Geom g;
+    g.X = p->dims[0]; g.Y = p->dims[1]; g.Z = p->dims[2]; g.T = p->dims[3];
+    g.Xh = g.X / 2;
+    g.Vh = (int)(V / 2);
+    g.Ls = p->Ls;
+    g.pad = 0;
+    g.tbc = (double)p->t_bc;
+    void* links[4][2];
+    size_t off = 0;
+    for (int pr = 0; pr < 4; ++pr)
+        for (int par = 0; par < 2; ++par) {
+            links[pr][par] = base + off;
+            off += kNaLinks[pr];
+        }
+    VecRef fin[2], fout[2];
+    for (int par = 0; par < 2; ++par) {
+        fin[par] = VecRef{base + off, nullptr};
+        off += kNaField;
+        fout[par] = VecRef{base + off, nullptr};
+        off += kNaField;
+    }
+    int* bad = reinterpret_cast<int*>(base + off);
+
+    // the flag must start at zero: the array keeps the previous call's contents
+    if (cudaMemsetAsync(bad, 0, sizeof(int), st) != cudaSuccess) return EOFA_ERR_CUDA;
+    if (gauge_import((const double*)gauge, g, links, bad, st) != cudaSuccess) return EOFA_ERR_CUDA;
+    int hbad = 0;
+    if (cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return EOFA_ERR_CUDA;
+    if (hbad) return EOFA_ERR_ARG;
+    for (int par = 0; par < 2; ++par)
+        if (layout_import(fin[par], (const double*)in, g, par, 0, st) != cudaSuccess) return EOFA_ERR_CUDA;
+    for (int par = 0; par < 2; ++par) {
+        HopArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.g = g;
+        a.out_par = par;
+        a.in = fin[1 - par].d;
+        a.y = fin[par].d;
+        a.out = fout[par].d;
+        a.lk_out = links[EOFA_F64][par];
+        a.lk_in = links[EOFA_F64][1 - par];
+        a.rd.fin = FIN_NONE;
+        if (launch_hop_f64(KIND_FULL, a, &k, st) != cudaSuccess) return EOFA_ERR_CUDA;
+    }
+    for (int par = 0; par < 2; ++par)
+        if (layout_export((double*)out, fout[par], g, par, 0, st) != cudaSuccess) return EOFA_ERR_CUDA;
+    return EOFA_OK;
+}
