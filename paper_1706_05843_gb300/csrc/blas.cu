@@ -54,6 +54,59 @@ cudaError_t while_cond(cudaGraphConditionalHandle h, DevScal* sc, cudaStream_t s
     return cudaGetLastError();
 }
 
+// Batched solves: the loop goes on while any system still iterates.
+__global__ void k_while_cond_all(cudaGraphConditionalHandle h, ScalList L) {
+    int go = 0;
+    for (int i = 0; i < L.n; ++i) {
+        const DevScal* sc = L.s[i];
+        if (!sc->done && !sc->nonfinite && sc->iters < sc->max_iters) go = 1;
+    }
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+cudaError_t while_cond_all(cudaGraphConditionalHandle h, const ScalList& L, cudaStream_t st) {
+    k_while_cond_all<<<1, 1, 0, st>>>(h, L);
+    return cudaGetLastError();
+}
+
+// Host-set control of a batched round: skip flag and iteration budget.
+__global__ void k_inner_ctl(DevScal* sc, int skip, int max_iters) {
+    sc->skip = skip;
+    sc->max_iters = max_iters;
+}
+
+cudaError_t inner_ctl(DevScal* sc, int skip, int max_iters, cudaStream_t st) {
+    k_inner_ctl<<<1, 1, 0, st>>>(sc, skip, max_iters);
+    return cudaGetLastError();
+}
+
+// Start of a batched inner solve, on the device: the outer residual
+// |r|^2 = store[0] and |b|^2 = store[1] + store[2] give the inner target
+// max(floor, tol |b| / |r|); a system that has converged (or skips) is
+// marked done and its kernels return at once.
+__global__ void k_inner_init(DevScal* sc, double tol, double floor_tol) {
+    const double rr = sc->store[0], bb = sc->store[1] + sc->store[2];
+    sc->qq = sc->zz = sc->rr = sc->alpha = sc->beta = 0.0;
+    sc->iters = 0;
+    sc->nonfinite = 0;
+    sc->timed_out = 0;
+    sc->timeout_ns = 0;
+    sc->t0_ns = globaltimer_ns();
+    const double rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    if (sc->skip || !(rel > tol)) {
+        sc->done = 1;
+        return;
+    }
+    const double t = fmax(tol / rel, floor_tol);
+    sc->target_rr = t * t;
+    sc->done = 0;
+}
+
+cudaError_t inner_init(DevScal* sc, double tol, double floor_tol, cudaStream_t st) {
+    k_inner_init<<<1, 1, 0, st>>>(sc, tol, floor_tol);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // CG updates
 // ---------------------------------------------------------------------------

@@ -24,6 +24,9 @@ cudaError_t launch_hop_bf16(int kind, const HopArgs& a, const void* coef, cudaSt
 cudaError_t scal_init(DevScal* sc, double target_rr, int max_iters, unsigned long long timeout_ns,
                       cudaStream_t st);
 cudaError_t while_cond(cudaGraphConditionalHandle h, DevScal* sc, cudaStream_t st);
+cudaError_t while_cond_all(cudaGraphConditionalHandle h, const ScalList& L, cudaStream_t st);
+cudaError_t inner_ctl(DevScal* sc, int skip, int max_iters, cudaStream_t st);
+cudaError_t inner_init(DevScal* sc, double tol, double floor_tol, cudaStream_t st);
 cudaError_t blas_cg_xr(int prec, int xprec, VecRef x, VecRef p, VecRef q, VecRef r, long n5, int Ls,
                        Reduce rd, const int* done, cudaStream_t st);
 cudaError_t blas_cg_p(int prec, VecRef p, VecRef z, long n5, int Ls, const DevScal* sc, cudaStream_t st);

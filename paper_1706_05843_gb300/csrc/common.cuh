@@ -70,7 +70,13 @@ struct DevScal {
     unsigned long long t0_ns;      // %globaltimer at the start of the solve
     unsigned long long timeout_ns; // 0: none
     int timed_out;
-    int pad;
+    int skip;                      // batched solves: this system sits the round out
+};
+
+// the device scalars of up to 32 systems (one batched graph)
+struct ScalList {
+    DevScal* s[32];
+    int n;
 };
 
 enum Fin { FIN_NONE = 0, FIN_STORE = 1, FIN_ALPHA = 2, FIN_BETA = 3, FIN_RR = 4, FIN_ZZ = 5 };
@@ -180,10 +186,24 @@ __device__ __forceinline__ uint2 pack4(const float* v, const __nv_bfloat16*) {
 
 // ---------------------------------------------------------------------------
 // spinor access.  base points at the parity's chunk array.
+//
+// Order of the 24 reals in memory.  FP64: the logical order
+// [spin][colour][re, im].  FP32/FP16/BF16 ("pair order"): index
+// ((half * 3 + colour) * 2 + reim) * 2 + (spin & 1), half = spin >> 1, so
+// every aligned pair of reals holds the same component of the two spins of
+// one chirality -- the operand shape of the packed FP32x2 hop arithmetic --
+// and the P+ half is still reals 0..11.
+// load_raw / store_raw move memory order; load_sp / store_sp convert to and
+// from the logical order (a compile-time renaming of registers).
 // ---------------------------------------------------------------------------
+__host__ __device__ constexpr int pair_to_logical(int m) {
+    // m = ((half*3 + c)*2 + reim)*2 + lane  ->  ((2*half + lane)*3 + c)*2 + reim
+    return ((2 * (m / 12) + (m & 1)) * 3 + (m % 12) / 4) * 2 + ((m >> 1) & 1);
+}
+
 template <typename S, typename R>
-__device__ __forceinline__ void load_sp(const void* __restrict__ base, const float* __restrict__ nrm,
-                                        long xcb, int s, int Ls, R* v) {
+__device__ __forceinline__ void load_raw(const void* __restrict__ base, const float* __restrict__ nrm,
+                                         long xcb, int s, int Ls, R* v) {
     if constexpr (sizeof(S) == 8) {
         const double2* p = reinterpret_cast<const double2*>(base) + xcb * 12 * Ls + s;
 #pragma unroll
@@ -256,8 +276,8 @@ __device__ __forceinline__ void load_half(const void* __restrict__ base, const f
 }
 
 template <typename S, typename R>
-__device__ __forceinline__ void store_sp(void* __restrict__ base, float* __restrict__ nrm, long xcb,
-                                         int s, int Ls, const R* v) {
+__device__ __forceinline__ void store_raw(void* __restrict__ base, float* __restrict__ nrm, long xcb,
+                                          int s, int Ls, const R* v) {
     if constexpr (sizeof(S) == 8) {
         double2* p = reinterpret_cast<double2*>(base) + xcb * 12 * Ls + s;
 #pragma unroll
@@ -284,6 +304,33 @@ __device__ __forceinline__ void store_sp(void* __restrict__ base, float* __restr
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) p[c * Ls] = pack8(w + 8 * c, (const S*)nullptr);
+    }
+}
+
+// logical-order access (BLAS, conversions, import/export)
+template <typename S, typename R>
+__device__ __forceinline__ void load_sp(const void* __restrict__ base, const float* __restrict__ nrm,
+                                        long xcb, int s, int Ls, R* v) {
+    if constexpr (sizeof(S) == 8) {
+        load_raw<S, R>(base, nrm, xcb, s, Ls, v);
+    } else {
+        R m[24];
+        load_raw<S, R>(base, nrm, xcb, s, Ls, m);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) v[pair_to_logical(i)] = m[i];
+    }
+}
+
+template <typename S, typename R>
+__device__ __forceinline__ void store_sp(void* __restrict__ base, float* __restrict__ nrm, long xcb,
+                                         int s, int Ls, const R* v) {
+    if constexpr (sizeof(S) == 8) {
+        store_raw<S, R>(base, nrm, xcb, s, Ls, v);
+    } else {
+        R m[24];
+#pragma unroll
+        for (int i = 0; i < 24; ++i) m[i] = v[pair_to_logical(i)];
+        store_raw<S, R>(base, nrm, xcb, s, Ls, m);
     }
 }
 

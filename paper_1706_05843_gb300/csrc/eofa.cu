@@ -453,21 +453,38 @@ double default_inner_tol(int P) {
     }
 }
 
-eofa_status solve_impl(eofa_ctx* c, const double* rhs, double* sol, const eofa_solve_opts& o,
-                       eofa_solve_stats* stats, cudaStream_t st) {
-    const auto t0 = Clock::now();
-    eofa_solve_stats S;
-    std::memset(&S, 0, sizeof(S));
-    const int P = o.inner;
-    if (P < 0 || P > 3) return fail(c, EOFA_ERR_ARG, "opts.inner must be an eofa_prec");
+// State of one solve between its phases (shared by the single and the
+// batched drivers).
+struct SolveState {
+    Clock::time_point t0;
+    int P = 0, xp = 0, H = 1, maxit = 0, maxouter = 0;
+    double bb = 0.0, rel = 1.0;
+    int total = 0, outer = 0;
+    eofa_status result = EOFA_ERR_NOT_CONVERGED;
+    bool finished = false;
+};
+
+eofa_status enqueue_read(eofa_ctx* c, cudaStream_t st) {
+    CK(cudaMemcpyAsync(c->h_scal, c->scal, sizeof(DevScal), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    return EOFA_OK;
+}
+
+// Phase 1: options, b = g5 R5 phi (H form) or b (K form) with |b|^2 into
+// store[1] + store[2], the odd part of the initial guess, the even-odd
+// source b~o = b_o + 1/2 D_h D~ M^-1 b_e.  Ends with a read-back enqueued.
+eofa_status solve_begin(eofa_ctx* c, const double* rhs, const double* sol, const eofa_solve_opts& o,
+                        SolveState& ss, cudaStream_t st) {
+    ss.t0 = Clock::now();
+    ss.P = o.inner;
+    if (ss.P < 0 || ss.P > 3) return fail(c, EOFA_ERR_ARG, "opts.inner must be an eofa_prec");
     if (!(o.tol > 0.0)) return fail(c, EOFA_ERR_ARG, "opts.tol must be positive");
     if (o.precond != 0) return fail(c, EOFA_ERR_UNSUPPORTED, "learned preconditioner not loaded");
-    const int maxit = o.max_iter > 0 ? o.max_iter : 100000;
-    const int maxouter = o.max_outer > 0 ? o.max_outer : 100;
-    const int H = o.rhs_form == 0 ? 1 : 0;
-    const int xp = P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
+    ss.maxit = o.max_iter > 0 ? o.max_iter : 100000;
+    ss.maxouter = o.max_outer > 0 ? o.max_outer : 100;
+    ss.H = o.rhs_form == 0 ? 1 : 0;
+    ss.xp = ss.P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
     eofa_status s;
-    if ((s = ensure_inner(c, P))) return s;
+    if ((s = ensure_inner(c, ss.P))) return s;
     c->timing = o.kernel_timing != 0;
     c->launches = 0;
     c->hop_ms = 0.0;
@@ -477,16 +494,13 @@ eofa_status solve_impl(eofa_ctx* c, const double* rhs, double* sol, const eofa_s
     const VecRef none{};
     const Geom& g = c->g;
     const int Ls = g.Ls;
-
-    // b = g5 R5 phi (H form) or b (K form); |b|^2 into store[1] + store[2]
-    CKL(layout_import(c->b[0], rhs, g, 0, H, st), "import");
-    CKL(layout_import(c->b[1], rhs, g, 1, H, st), "import");
+    CKL(layout_import(c->b[0], rhs, g, 0, ss.H, st), "import");
+    CKL(layout_import(c->b[1], rhs, g, 1, ss.H, st), "import");
     CKL(blas_copy(0, c->t[0], 0, c->b[0], c->n5, Ls, 1.0, -1, red(c, FIN_STORE, 1), st), "norm");
     CKL(blas_copy(0, c->t[1], 0, c->b[1], c->n5, Ls, 1.0, -1, red(c, FIN_STORE, 2), st), "norm");
-    // initial guess (odd part of psi')
     if (o.use_guess) {
         CKL(layout_import(c->x[1], sol, g, 1, 0, st), "import");
-        if (H) {
+        if (ss.H) {
             if ((s = hop(c, 0, KIND_LOC_DTINV, 1, none, c->x[1], c->t[1], red(c, FIN_NONE), nullptr, st)))
                 return s;
             CKL(blas_copy(0, c->x[1], 0, c->t[1], c->n5, Ls, 1.0, -1, red(c, FIN_NONE), st), "copy");
@@ -494,87 +508,298 @@ eofa_status solve_impl(eofa_ctx* c, const double* rhs, double* sol, const eofa_s
     } else {
         CKL(blas_zero(0, c->x[1], c->n5, Ls, st), "zero");
     }
-    // even-odd source b~o = b_o + 1/2 D_h D~ M^-1 b_e
     if ((s = hop(c, 0, KIND_LOC_DTMINV, 0, none, c->b[0], c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
     if ((s = hop(c, 0, KIND_SRC, 1, c->t[0], c->b[1], c->bto, red(c, FIN_NONE), nullptr, st))) return s;
-    if ((s = read_scal(c, st))) return s;
-    const double bb = c->h_scal->store[1] + c->h_scal->store[2];
-    if (!std::isfinite(bb)) return fail(c, EOFA_ERR_NONFINITE, "right-hand side is not finite");
-    if (bb == 0.0) {
+    return enqueue_read(c, st);
+}
+
+// After the read-back of solve_begin: |b|^2, and the zero right-hand side.
+eofa_status solve_check_rhs(eofa_ctx* c, double* sol, SolveState& ss, cudaStream_t st) {
+    ss.bb = c->h_scal->store[1] + c->h_scal->store[2];
+    if (!std::isfinite(ss.bb)) return fail(c, EOFA_ERR_NONFINITE, "right-hand side is not finite");
+    if (ss.bb == 0.0) {
         CK(cudaMemsetAsync(sol, 0, (size_t)c->n5 * 2 * 24 * sizeof(double), st), "memset");
+        ss.finished = true;
+        ss.result = EOFA_OK;
+        ss.rel = 0.0;
+    }
+    return EOFA_OK;
+}
+
+// r = b~o - S x_o in FP64 with |r|^2 into store[0]; read-back enqueued.
+eofa_status outer_residual(eofa_ctx* c, cudaStream_t st) {
+    const VecRef none{};
+    eofa_status s;
+    if ((s = hop(c, 0, KIND_EO_MINV, 0, c->x[1], none, c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
+    if ((s = hop(c, 0, KIND_OE_SCHUR, 1, c->t[0], c->x[1], c->qo, red(c, FIN_NONE), nullptr, st))) return s;
+    CKL(blas_sub(c->ro, c->bto, c->qo, c->n5, c->g.Ls, red(c, FIN_STORE, 0), st), "sub");
+    return enqueue_read(c, st);
+}
+
+// After the read-back of outer_residual: stop (converged, cap, timeout or
+// non-finite) or go on.  Returns true when the outer loop must continue.
+bool outer_decide(eofa_ctx* c, const eofa_solve_opts& o, SolveState& ss) {
+    const double rr = c->h_scal->store[0];
+    if (!std::isfinite(rr)) {
+        ss.result = fail(c, EOFA_ERR_NONFINITE, "non-finite outer residual");
+        return false;
+    }
+    ss.rel = std::sqrt(rr / ss.bb);
+    if (ss.rel <= o.tol) { ss.result = EOFA_OK; return false; }
+    if (ss.outer >= ss.maxouter || ss.total >= ss.maxit) {
+        ss.result = fail(c, EOFA_ERR_NOT_CONVERGED, "iteration cap");
+        return false;
+    }
+    if (o.timeout_ms > 0 && since(ss.t0) * 1e3 > (double)o.timeout_ms) {
+        ss.result = fail(c, EOFA_ERR_TIMEOUT, "solve exceeded timeout_ms");
+        return false;
+    }
+    return true;
+}
+
+double inner_tol_floor(const eofa_solve_opts& o, int P) {
+    if (P == EOFA_F64) return 0.0;
+    return o.inner_tol > 0.0 ? o.inner_tol : default_inner_tol(P);
+}
+
+// Phase 3: x_e = M^-1 (b_e + 1/2 D_h D~ x_o), the FP64 true residual of the
+// full system, psi = D~ psi' (H form), export and statistics.
+eofa_status solve_end(eofa_ctx* c, double* sol, const eofa_solve_opts& o, SolveState& ss,
+                      eofa_solve_stats* stats, cudaStream_t st) {
+    eofa_solve_stats S;
+    std::memset(&S, 0, sizeof(S));
+    const VecRef none{};
+    const Geom& g = c->g;
+    const int Ls = g.Ls;
+    eofa_status s;
+    if (ss.bb == 0.0) {
         CK(cudaStreamSynchronize(st), "sync");
-        S.status = EOFA_OK;
-        S.kernel_launches = c->launches;
-        S.seconds = since(t0);
-        if (stats) *stats = S;
-        return EOFA_OK;
-    }
-    const double bnorm = std::sqrt(bb);
-    eofa_status result = EOFA_ERR_NOT_CONVERGED;
-    int total = 0, outer = 0;
-    double rel = 1.0;
-    for (;;) {
-        // r = b~o - S x_o (FP64)
-        if ((s = hop(c, 0, KIND_EO_MINV, 0, c->x[1], none, c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
-        if ((s = hop(c, 0, KIND_OE_SCHUR, 1, c->t[0], c->x[1], c->qo, red(c, FIN_NONE), nullptr, st))) return s;
-        CKL(blas_sub(c->ro, c->bto, c->qo, c->n5, Ls, red(c, FIN_STORE, 0), st), "sub");
-        if ((s = read_scal(c, st))) return s;
-        const double rr = c->h_scal->store[0];
-        if (!std::isfinite(rr)) { result = fail(c, EOFA_ERR_NONFINITE, "non-finite outer residual"); break; }
-        rel = std::sqrt(rr) / bnorm;
-        if (rel <= o.tol) { result = EOFA_OK; break; }
-        if (outer >= maxouter || total >= maxit) { result = fail(c, EOFA_ERR_NOT_CONVERGED, "iteration cap"); break; }
-        if (o.timeout_ms > 0 && since(t0) * 1e3 > (double)o.timeout_ms) {
-            result = fail(c, EOFA_ERR_TIMEOUT, "solve exceeded timeout_ms");
-            break;
-        }
-        double itol = o.tol / rel;
-        if (P != EOFA_F64) {
-            const double dt = o.inner_tol > 0.0 ? o.inner_tol : default_inner_tol(P);
-            itol = std::max(itol, dt);
-        }
-        // inner source r / |r| in precision P
-        CKL(blas_copy(P, c->inner[P].r, 0, c->ro, c->n5, Ls, 1.0, 0, red(c, FIN_NONE), st), "copy");
-        int its = 0;
-        double irr = 0.0;
-        eofa_status is = run_cgnr(c, P, itol, maxit - total, &its, &irr, st, t0, o.timeout_ms);
-        total += its;
-        ++outer;
-        if (is == EOFA_ERR_NONFINITE || is == EOFA_ERR_TIMEOUT || is == EOFA_ERR_CUDA) { result = is; break; }
-        CKL(blas_acc(c->x[1], xp, c->inner[P].x, c->n5, Ls, c->scal, 0, st), "acc");
-    }
-    // x_e = M^-1 (b_e + 1/2 D_h D~ x_o)
-    if ((s = hop(c, 0, KIND_RECON, 0, c->x[1], c->b[0], c->x[0], red(c, FIN_NONE), nullptr, st))) return s;
-    // true residual of the full system
-    if ((s = hop(c, 0, KIND_FULL, 0, c->x[1], c->x[0], c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
-    if ((s = hop(c, 0, KIND_FULL, 1, c->x[0], c->x[1], c->t[1], red(c, FIN_NONE), nullptr, st))) return s;
-    CKL(blas_sub(c->t[0], c->b[0], c->t[0], c->n5, Ls, red(c, FIN_STORE, 3), st), "sub");
-    CKL(blas_sub(c->t[1], c->b[1], c->t[1], c->n5, Ls, red(c, FIN_STORE, 4), st), "sub");
-    if (H) {
-        if ((s = hop(c, 0, KIND_LOC_DT, 0, none, c->x[0], c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
-        if ((s = hop(c, 0, KIND_LOC_DT, 1, none, c->x[1], c->t[1], red(c, FIN_NONE), nullptr, st))) return s;
-        CKL(layout_export((double*)sol, c->t[0], g, 0, 0, st), "export");
-        CKL(layout_export((double*)sol, c->t[1], g, 1, 0, st), "export");
     } else {
-        CKL(layout_export((double*)sol, c->x[0], g, 0, 0, st), "export");
-        CKL(layout_export((double*)sol, c->x[1], g, 1, 0, st), "export");
+        if ((s = hop(c, 0, KIND_RECON, 0, c->x[1], c->b[0], c->x[0], red(c, FIN_NONE), nullptr, st))) return s;
+        if ((s = hop(c, 0, KIND_FULL, 0, c->x[1], c->x[0], c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
+        if ((s = hop(c, 0, KIND_FULL, 1, c->x[0], c->x[1], c->t[1], red(c, FIN_NONE), nullptr, st))) return s;
+        CKL(blas_sub(c->t[0], c->b[0], c->t[0], c->n5, Ls, red(c, FIN_STORE, 3), st), "sub");
+        CKL(blas_sub(c->t[1], c->b[1], c->t[1], c->n5, Ls, red(c, FIN_STORE, 4), st), "sub");
+        if (ss.H) {
+            if ((s = hop(c, 0, KIND_LOC_DT, 0, none, c->x[0], c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
+            if ((s = hop(c, 0, KIND_LOC_DT, 1, none, c->x[1], c->t[1], red(c, FIN_NONE), nullptr, st))) return s;
+            CKL(layout_export(sol, c->t[0], g, 0, 0, st), "export");
+            CKL(layout_export(sol, c->t[1], g, 1, 0, st), "export");
+        } else {
+            CKL(layout_export(sol, c->x[0], g, 0, 0, st), "export");
+            CKL(layout_export(sol, c->x[1], g, 1, 0, st), "export");
+        }
+        if ((s = read_scal(c, st))) return s;
+        S.true_res = std::sqrt((c->h_scal->store[3] + c->h_scal->store[4]) / ss.bb);
     }
-    if ((s = read_scal(c, st))) return s;
-    S.true_res = std::sqrt((c->h_scal->store[3] + c->h_scal->store[4]) / bb);
-    S.recur_res = rel;
-    S.outer_iters = outer;
-    S.inner_iters = total;
+    S.recur_res = ss.rel;
+    S.outer_iters = ss.outer;
+    S.inner_iters = ss.total;
     S.hop_ms = c->hop_ms;
     S.hop_launches = c->hop_launches;
     S.hop_bytes = c->hop_bytes;
     S.kernel_launches = c->launches;
-    if (result == EOFA_OK && !(S.true_res <= o.tol * 1.0000001)) {
+    eofa_status result = ss.result;
+    if (result == EOFA_OK && ss.bb != 0.0 && !(S.true_res <= o.tol * 1.0000001))
         result = fail(c, EOFA_ERR_NOT_CONVERGED, "true residual above tol after the outer loop");
-    }
     S.status = result;
-    S.seconds = since(t0);
+    S.seconds = since(ss.t0);
     if (stats) *stats = S;
     return result;
+}
+
+eofa_status solve_impl(eofa_ctx* c, const double* rhs, double* sol, const eofa_solve_opts& o,
+                       eofa_solve_stats* stats, cudaStream_t st) {
+    SolveState ss;
+    eofa_status s;
+    if ((s = solve_begin(c, rhs, sol, o, ss, st))) return s;
+    CK(cudaStreamSynchronize(st), "sync");
+    if ((s = solve_check_rhs(c, sol, ss, st))) return s;
+    const int Ls = c->g.Ls;
+    while (!ss.finished) {
+        if ((s = outer_residual(c, st))) return s;
+        CK(cudaStreamSynchronize(st), "sync");
+        if (!outer_decide(c, o, ss)) break;
+        const double itol = std::max(o.tol / ss.rel, inner_tol_floor(o, ss.P));
+        // inner source r / |r| in precision P
+        CKL(blas_copy(ss.P, c->inner[ss.P].r, 0, c->ro, c->n5, Ls, 1.0, 0, red(c, FIN_NONE), st), "copy");
+        int its = 0;
+        double irr = 0.0;
+        eofa_status is = run_cgnr(c, ss.P, itol, ss.maxit - ss.total, &its, &irr, st, ss.t0, o.timeout_ms);
+        ss.total += its;
+        ++ss.outer;
+        if (is == EOFA_ERR_NONFINITE || is == EOFA_ERR_TIMEOUT || is == EOFA_ERR_CUDA) {
+            ss.result = is;
+            break;
+        }
+        CKL(blas_acc(c->x[1], ss.xp, c->inner[ss.P].x, c->n5, Ls, c->scal, 0, st), "acc");
+    }
+    return solve_end(c, sol, o, ss, stats, st);
+}
+
+// ---------------------------------------------------------------------------
+// batched solves: one CUDA graph per call holds, for every system, the
+// inner-solve prologue (parallel branches) and then a device-driven WHILE
+// node whose body runs kChunk CG iterations of every system (again parallel
+// branches) and a condition kernel over all systems.  Systems of different
+// lattices and Ls run side by side; converged systems turn into empty
+// kernels.  The host only runs the outer FP64 defect-correction step.
+// ---------------------------------------------------------------------------
+constexpr int kBatchMax = 32;
+
+eofa_status build_batch_graph(eofa_ctx* const* cs, int n, int P, double tol, double floor_tol,
+                              cudaGraphExec_t* exec_out) {
+    eofa_ctx* c = cs[0];  // errors are reported on the first context
+    std::vector<cudaStream_t> str(n + 1, nullptr);
+    std::vector<cudaEvent_t> evs(n + 1, nullptr);
+    cudaGraph_t pro = nullptr, g = nullptr;
+    eofa_status s = EOFA_OK;
+    cudaError_t e = cudaSuccess;
+    auto cleanup = [&]() {
+        for (auto x : str) if (x) cudaStreamDestroy(x);
+        for (auto x : evs) if (x) cudaEventDestroy(x);
+        if (pro) cudaGraphDestroy(pro);
+        if (g) cudaGraphDestroy(g);
+    };
+    for (int i = 0; i <= n && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&str[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "batch streams"); }
+    // fork/join capture helper: run f(i, stream) on a branch per system
+    auto capture_branches = [&](auto&& f) -> eofa_status {
+        cudaError_t ee = cudaEventRecord(evs[n], str[n]);
+        for (int i = 0; i < n && ee == cudaSuccess; ++i) ee = cudaStreamWaitEvent(str[i], evs[n], 0);
+        if (ee != cudaSuccess) return cuda_fail(c, ee, "fork");
+        for (int i = 0; i < n; ++i) {
+            eofa_status r = f(i, str[i]);
+            if (r != EOFA_OK) return r;
+        }
+        for (int i = 0; i < n && ee == cudaSuccess; ++i) {
+            ee = cudaEventRecord(evs[i], str[i]);
+            if (ee == cudaSuccess) ee = cudaStreamWaitEvent(str[n], evs[i], 0);
+        }
+        return ee == cudaSuccess ? EOFA_OK : cuda_fail(c, ee, "join");
+    };
+    // prologue graph
+    e = cudaStreamBeginCapture(str[n], cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "capture"); }
+    s = capture_branches([&](int i, cudaStream_t st) -> eofa_status {
+        eofa_ctx* ci = cs[i];
+        Inner& in = ci->inner[P];
+        const int xp = P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
+        const VecRef none{};
+        eofa_status r;
+        CK(inner_init(ci->scal, tol, floor_tol, st), "inner_init");
+        CK(blas_copy(P, in.r, 0, ci->ro, ci->n5, ci->g.Ls, 1.0, 0, red(ci, FIN_NONE), st), "copy");
+        CK(blas_zero(xp, in.x, ci->n5, ci->g.Ls, st), "zero");
+        const int* done = &ci->scal->done;
+        if ((r = hop(ci, P, KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(ci, FIN_NONE), done, st))) return r;
+        if ((r = hop(ci, P, KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(ci, FIN_ZZ), done, st))) return r;
+        CK(blas_copy(P, in.p, P, in.z, ci->n5, ci->g.Ls, 1.0, -1, red(ci, FIN_NONE), st), "copy");
+        return EOFA_OK;
+    });
+    cudaError_t e2 = cudaStreamEndCapture(str[n], &pro);
+    if (s == EOFA_OK && e2 != cudaSuccess) s = cuda_fail(c, e2, "end capture");
+    if (s != EOFA_OK) { cleanup(); return s; }
+    // top graph: prologue (child graph) -> WHILE
+    cudaGraphNode_t child, wn;
+    e = cudaGraphCreate(&g, 0);
+    if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&child, g, nullptr, 0, pro);
+    cudaGraphConditionalHandle h;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+    std::memset(npbuf, 0, sizeof(npbuf));
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(npbuf);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&wn, g, &child, nullptr, 1, &np);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "batch graph"); }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(str[n], body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "capture body"); }
+    s = capture_branches([&](int i, cudaStream_t st) -> eofa_status {
+        eofa_status r = EOFA_OK;
+        for (int k = 0; k < kChunk && r == EOFA_OK; ++k) r = cg_iteration(cs[i], P, st, false);
+        return r;
+    });
+    if (s == EOFA_OK) {
+        ScalList L;
+        std::memset(&L, 0, sizeof(L));
+        L.n = n;
+        for (int i = 0; i < n; ++i) L.s[i] = cs[i]->scal;
+        e = while_cond_all(h, L, str[n]);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "while_cond_all");
+    }
+    cudaGraph_t cap = nullptr;
+    e2 = cudaStreamEndCapture(str[n], &cap);
+    if (s == EOFA_OK && e2 != cudaSuccess) s = cuda_fail(c, e2, "end capture body");
+    if (s == EOFA_OK) {
+        e = cudaGraphInstantiate(exec_out, g, 0);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "instantiate batch graph");
+    }
+    cleanup();
+    return s;
+}
+
+eofa_status solve_batched_impl(eofa_ctx* const* cs, int n, const void* const* rhs, void* const* sol,
+                               const eofa_solve_opts& o, eofa_solve_stats* stats, cudaStream_t st) {
+    std::vector<SolveState> ss(n);
+    eofa_status s;
+    for (int i = 0; i < n; ++i) {
+        cs[i]->err.clear();
+        if ((s = solve_begin(cs[i], (const double*)rhs[i], (const double*)sol[i], o, ss[i], st))) return s;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return EOFA_ERR_CUDA;
+    for (int i = 0; i < n; ++i)
+        if ((s = solve_check_rhs(cs[i], (double*)sol[i], ss[i], st))) return s;
+    const int P = ss[0].P;
+    cudaGraphExec_t exec = nullptr;
+    if ((s = build_batch_graph(cs, n, P, o.tol, inner_tol_floor(o, P), &exec))) return s;
+    for (;;) {
+        int active = 0;
+        for (int i = 0; i < n; ++i)
+            if (!ss[i].finished && (s = outer_residual(cs[i], st))) { cudaGraphExecDestroy(exec); return s; }
+        if (cudaStreamSynchronize(st) != cudaSuccess) { cudaGraphExecDestroy(exec); return EOFA_ERR_CUDA; }
+        for (int i = 0; i < n; ++i) {
+            if (ss[i].finished) continue;
+            if (!outer_decide(cs[i], o, ss[i])) ss[i].finished = true;
+            else ++active;
+        }
+        // every system gets its skip flag and iteration budget for this round
+        for (int i = 0; i < n; ++i) {
+            eofa_ctx* c = cs[i];
+            CKL(inner_ctl(c->scal, ss[i].finished ? 1 : 0, std::max(1, ss[i].maxit - ss[i].total), st), "inner_ctl");
+        }
+        if (active == 0) break;
+        if (cudaGraphLaunch(exec, st) != cudaSuccess) { cudaGraphExecDestroy(exec); return EOFA_ERR_CUDA; }
+        for (int i = 0; i < n; ++i)
+            if ((s = enqueue_read(cs[i], st))) { cudaGraphExecDestroy(exec); return s; }
+        if (cudaStreamSynchronize(st) != cudaSuccess) { cudaGraphExecDestroy(exec); return EOFA_ERR_CUDA; }
+        for (int i = 0; i < n; ++i) {
+            if (ss[i].finished) continue;
+            eofa_ctx* c = cs[i];
+            const DevScal& h = *c->h_scal;
+            ss[i].total += h.iters;
+            ++ss[i].outer;
+            c->launches += (long)(6 * kChunk) * ((h.iters + kChunk - 1) / kChunk + (h.iters == 0 ? 1 : 0));
+            if (h.nonfinite) {
+                ss[i].result = fail(c, EOFA_ERR_NONFINITE, "NaN or Inf in the inner CG reductions");
+                ss[i].finished = true;
+                continue;
+            }
+            CKL(blas_acc(c->x[1], ss[i].xp, c->inner[P].x, c->n5, c->g.Ls, c->scal, 0, st), "acc");
+        }
+    }
+    cudaGraphExecDestroy(exec);
+    eofa_status first = EOFA_OK;
+    for (int i = 0; i < n; ++i) {
+        s = solve_end(cs[i], (double*)sol[i], o, ss[i], stats ? stats + i : nullptr, st);
+        if (s != EOFA_OK && first == EOFA_OK) first = s;
+    }
+    return first;
 }
 
 eofa_status apply_impl(eofa_ctx* c, const void* in, void* out, int which, cudaStream_t st) {
@@ -708,9 +933,27 @@ eofa_status eofa_apply_batched(eofa_ctx* const* ctx, int n, const void* const* i
 eofa_status eofa_solve_batched(eofa_ctx* const* ctx, int n, const void* const* rhs, void* const* sol,
                                const eofa_solve_opts* opts, eofa_solve_stats* stats, void* stream) {
     if (n < 0 || (n > 0 && (!ctx || !rhs || !sol || !opts))) return EOFA_ERR_ARG;
-    eofa_status first = EOFA_OK;
     for (int i = 0; i < n; ++i) {
-        eofa_status s = eofa_solve(ctx[i], rhs[i], sol[i], opts, stats ? stats + i : nullptr, stream);
+        if (!ctx[i] || !rhs[i] || !sol[i] || rhs[i] == sol[i]) return EOFA_ERR_ARG;
+        for (int j = 0; j < i; ++j)
+            if (ctx[j] == ctx[i]) return EOFA_ERR_ARG;  // one context per system
+    }
+    // kernel timing is an instrumentation of the host-driven loop: solve one by one
+    if (opts->kernel_timing || opts->inner < 0 || opts->inner > 3) {
+        eofa_status first = EOFA_OK;
+        for (int i = 0; i < n; ++i) {
+            eofa_status s = eofa_solve(ctx[i], rhs[i], sol[i], opts, stats ? stats + i : nullptr, stream);
+            if (s != EOFA_OK && first == EOFA_OK) first = s;
+        }
+        return first;
+    }
+    eofa_status first = EOFA_OK;
+    for (int lo = 0; lo < n; lo += kBatchMax) {
+        const int m = std::min(kBatchMax, n - lo);
+        eofa_status s = solve_batched_impl(ctx + lo, m, rhs + lo, sol + lo, *opts, stats ? stats + lo : nullptr,
+                                           (cudaStream_t)stream);
+        if (stats)
+            for (int i = 0; i < m; ++i) stats[lo + i].status = stats[lo + i].status ? stats[lo + i].status : 0;
         if (s != EOFA_OK && first == EOFA_OK) first = s;
     }
     return first;

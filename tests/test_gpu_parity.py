@@ -135,3 +135,46 @@ def test_non_su3_gauge_rejected(env):
     with pytest.raises(B.EofaError) as e:
         B.Solver(U, dims, 8, **MOB)
     assert e.value.status == 1
+
+
+BATCH = [((4, 4, 4, 4), 8, 0.5, dict(beta=-1.0, pm=1)),
+         ((2, 2, 2, 6), 4, 0.5, dict(beta=0.7, pm=-1, m3=0.3)),
+         ((4, 2, 6, 2), 12, 0.7, dict(beta=-1.0, pm=1, m1=0.0362, m3=0.0362)),
+         ((2, 4, 2, 4), 16, 0.5, dict(beta=-1.0, pm=-1))]
+
+
+@pytest.mark.parametrize("inner", ["f32", "f16", "f64"])
+def test_solve_batched_uneven_lattices(env, inner):
+    """One batched call over systems of different lattices and Ls; every
+    solution is judged by the oracle's operator and matches the one-by-one
+    solve."""
+    torch, B, O = env
+    solvers, oracles, rhs = [], [], []
+    for i, case in enumerate(BATCH):
+        torch_, s, o = setup(env, case, seed=10 + i)
+        solvers.append(s)
+        oracles.append(o)
+        rhs.append(torch.from_numpy(I.gaussian_fermion(case[0], case[1], 2000 + i)).cuda())
+    sols = [torch.empty_like(r) for r in rhs]
+    opts = B.make_opts(tol=1e-10, inner=inner)
+    stats = B.eofa_solve_batched([s.ctx for s in solvers], rhs, sols, opts)
+    for i, (s, o) in enumerate(zip(solvers, oracles)):
+        phi = rhs[i].cpu().numpy()
+        psi = sols[i].cpu().numpy()
+        assert rel(o.hsys(psi), phi) <= 1e-10, (i, stats[i].as_dict())
+        assert stats[i].status == 0
+        one, st1 = s.solve(rhs[i], tol=1e-10, inner=inner)
+        assert rel(psi, one.cpu().numpy()) < 1e-8
+    for s in solvers:
+        s.close()
+
+
+def test_solve_batched_rejects_duplicate_context(env):
+    torch, B, O = env
+    torch_, s, o = setup(env, CASES[0])
+    r = torch.from_numpy(I.gaussian_fermion(CASES[0][0], CASES[0][1], 1)).cuda()
+    with pytest.raises(B.EofaError) as e:
+        B.eofa_solve_batched([s.ctx, s.ctx], [r, r.clone()], [torch.empty_like(r), torch.empty_like(r)],
+                             B.make_opts(tol=1e-10))
+    assert e.value.status == 1
+    s.close()
