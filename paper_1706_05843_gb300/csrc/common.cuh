@@ -185,22 +185,9 @@ __device__ __forceinline__ uint2 pack4(const float* v, const __nv_bfloat16*) {
 }
 
 // ---------------------------------------------------------------------------
-// spinor access.  base points at the parity's chunk array.
-//
-// Order of the 24 reals in memory.  FP64: the logical order
-// [spin][colour][re, im].  FP32/FP16/BF16 ("pair order"): index
-// ((half * 3 + colour) * 2 + reim) * 2 + (spin & 1), half = spin >> 1, so
-// every aligned pair of reals holds the same component of the two spins of
-// one chirality -- the operand shape of the packed FP32x2 hop arithmetic --
-// and the P+ half is still reals 0..11.
-// load_raw / store_raw move memory order; load_sp / store_sp convert to and
-// from the logical order (a compile-time renaming of registers).
+// spinor access.  base points at the parity's chunk array; the 24 reals of a
+// spinor are in the logical order [spin][colour][re, im] in every precision.
 // ---------------------------------------------------------------------------
-__host__ __device__ constexpr int pair_to_logical(int m) {
-    // m = ((half*3 + c)*2 + reim)*2 + lane  ->  ((2*half + lane)*3 + c)*2 + reim
-    return ((2 * (m / 12) + (m & 1)) * 3 + (m % 12) / 4) * 2 + ((m >> 1) & 1);
-}
-
 template <typename S, typename R>
 __device__ __forceinline__ void load_raw(const void* __restrict__ base, const float* __restrict__ nrm,
                                          long xcb, int s, int Ls, R* v) {
@@ -307,31 +294,16 @@ __device__ __forceinline__ void store_raw(void* __restrict__ base, float* __rest
     }
 }
 
-// logical-order access (BLAS, conversions, import/export)
 template <typename S, typename R>
 __device__ __forceinline__ void load_sp(const void* __restrict__ base, const float* __restrict__ nrm,
                                         long xcb, int s, int Ls, R* v) {
-    if constexpr (sizeof(S) == 8) {
-        load_raw<S, R>(base, nrm, xcb, s, Ls, v);
-    } else {
-        R m[24];
-        load_raw<S, R>(base, nrm, xcb, s, Ls, m);
-#pragma unroll
-        for (int i = 0; i < 24; ++i) v[pair_to_logical(i)] = m[i];
-    }
+    load_raw<S, R>(base, nrm, xcb, s, Ls, v);
 }
 
 template <typename S, typename R>
 __device__ __forceinline__ void store_sp(void* __restrict__ base, float* __restrict__ nrm, long xcb,
                                          int s, int Ls, const R* v) {
-    if constexpr (sizeof(S) == 8) {
-        store_raw<S, R>(base, nrm, xcb, s, Ls, v);
-    } else {
-        R m[24];
-#pragma unroll
-        for (int i = 0; i < 24; ++i) m[i] = v[pair_to_logical(i)];
-        store_raw<S, R>(base, nrm, xcb, s, Ls, m);
-    }
+    store_raw<S, R>(base, nrm, xcb, s, Ls, v);
 }
 
 // ---------------------------------------------------------------------------

@@ -306,120 +306,6 @@ __device__ __forceinline__ void op_MinvT(C2<R>* v, const SCoef<R>& c, bool sh) {
 }
 
 // ---------------------------------------------------------------------------
-// packed FP32x2 arithmetic (fma/add/mul.rn.f32x2, sm_100 and later)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return d;
-}
-__device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-__device__ __forceinline__ float2 f2add(float2 a, float2 b) {
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-__device__ __forceinline__ float2 f2swap(float2 a) { return make_float2(a.y, a.x); }
-
-// One hopping direction in pair order: p holds the neighbour spinor, pair
-// k = (half*3 + c)*2 + reim covering the spins (2 half, 2 half + 1); lk the
-// link as (re, re, im, im) per entry; au, ad accumulate the upper and lower
-// spin pairs.  Same algebra as hop_dir: h = psi_up + SG B psi_dn,
-// w = W h (W = U or U^dag), upper += ph w, lower += ph SG B^dag w.
-template <int MU, int SG, bool ADJ>
-__device__ __forceinline__ void hop_dir2(float2* __restrict__ au, float2* __restrict__ ad,
-                                         const float* __restrict__ p, const float4* __restrict__ lk,
-                                         float ph) {
-    constexpr float s = (float)SG;
-    float2 Hr[3], Hi[3], Hn[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float2 ur = make_float2(p[4 * c], p[4 * c + 1]);
-        const float2 ui = make_float2(p[4 * c + 2], p[4 * c + 3]);
-        const float2 dr = make_float2(p[12 + 4 * c], p[12 + 4 * c + 1]);
-        const float2 di = make_float2(p[12 + 4 * c + 2], p[12 + 4 * c + 3]);
-        if constexpr (MU == 0) {        // (h0, h1) = psi_up + s (-i psi3, -i psi2)
-            Hr[c] = f2fma(make_float2(s, s), f2swap(di), ur);
-            Hi[c] = f2fma(make_float2(-s, -s), f2swap(dr), ui);
-        } else if constexpr (MU == 1) { // psi_up + s (-psi3, psi2)
-            Hr[c] = f2fma(make_float2(-s, s), f2swap(dr), ur);
-            Hi[c] = f2fma(make_float2(-s, s), f2swap(di), ui);
-        } else if constexpr (MU == 2) { // psi_up + s (-i psi2, i psi3)
-            Hr[c] = f2fma(make_float2(s, -s), di, ur);
-            Hi[c] = f2fma(make_float2(-s, s), dr, ui);
-        } else {                        // psi_up + s psi_dn
-            Hr[c] = f2fma(make_float2(s, s), dr, ur);
-            Hi[c] = f2fma(make_float2(s, s), di, ui);
-        }
-        // negated operand for the minus-sign products of the complex multiply
-        Hn[c] = ADJ ? f2mul(make_float2(-1.f, -1.f), Hr[c]) : f2mul(make_float2(-1.f, -1.f), Hi[c]);
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float2 wr, wi;
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const float4 e = ADJ ? lk[b * 3 + a] : lk[a * 3 + b];
-            const float2 urr = make_float2(e.x, e.y), uii = make_float2(e.z, e.w);
-            if constexpr (!ADJ) {  // w = U h: wr = ur hr - ui hi, wi = ur hi + ui hr
-                wr = (b == 0) ? f2mul(urr, Hr[b]) : f2fma(urr, Hr[b], wr);
-                wi = (b == 0) ? f2mul(urr, Hi[b]) : f2fma(urr, Hi[b], wi);
-                wr = f2fma(uii, Hn[b], wr);
-                wi = f2fma(uii, Hr[b], wi);
-            } else {               // w = U^dag h: wr = ur hr + ui hi, wi = ur hi - ui hr
-                wr = (b == 0) ? f2mul(urr, Hr[b]) : f2fma(urr, Hr[b], wr);
-                wi = (b == 0) ? f2mul(urr, Hi[b]) : f2fma(urr, Hi[b], wi);
-                wr = f2fma(uii, Hi[b], wr);
-                wi = f2fma(uii, Hn[b], wi);
-            }
-        }
-        const float2 pp = make_float2(ph, ph);
-        au[2 * a] = f2fma(pp, wr, au[2 * a]);
-        au[2 * a + 1] = f2fma(pp, wi, au[2 * a + 1]);
-        const float q = s * ph;
-        if constexpr (MU == 0) {        // lower += s (i w1, i w0)
-            ad[2 * a] = f2fma(make_float2(-q, -q), f2swap(wi), ad[2 * a]);
-            ad[2 * a + 1] = f2fma(make_float2(q, q), f2swap(wr), ad[2 * a + 1]);
-        } else if constexpr (MU == 1) { // lower += s (w1, -w0)
-            ad[2 * a] = f2fma(make_float2(q, -q), f2swap(wr), ad[2 * a]);
-            ad[2 * a + 1] = f2fma(make_float2(q, -q), f2swap(wi), ad[2 * a + 1]);
-        } else if constexpr (MU == 2) { // lower += s (i w0, -i w1)
-            ad[2 * a] = f2fma(make_float2(-q, q), wi, ad[2 * a]);
-            ad[2 * a + 1] = f2fma(make_float2(q, -q), wr, ad[2 * a + 1]);
-        } else {                        // lower += s w
-            ad[2 * a] = f2fma(make_float2(q, q), wr, ad[2 * a]);
-            ad[2 * a + 1] = f2fma(make_float2(q, q), wi, ad[2 * a + 1]);
-        }
-    }
-}
-
-// offset of the real part of complex component cc = spin*3 + colour in a
-// staged row (memory order of the precision), and the step to its imaginary part
-template <typename R>
-__device__ __forceinline__ int col_off(int cc) {
-    if constexpr (sizeof(R) == 8) {
-        return 2 * cc;
-    } else {
-        const int sp = cc / 3, c = cc - 3 * sp;
-        return (((sp >> 1) * 3 + c) * 2) * 2 + (sp & 1);
-    }
-}
-template <typename R> struct ImStep { static constexpr int V = sizeof(R) == 8 ? 1 : 2; };
-
-// ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
 template <typename R> struct ShStride;
@@ -428,7 +314,7 @@ template <> struct ShStride<double> { static constexpr int V = 26; };  // 208 B 
 
 // one staged link: 18 reals padded to a multiple of 16 bytes
 template <typename R> struct LinkStride;
-template <> struct LinkStride<float> { static constexpr int V = 36; };   // 9 x (re, re, im, im)
+template <> struct LinkStride<float> { static constexpr int V = 20; };
 template <> struct LinkStride<double> { static constexpr int V = 18; };
 
 template <int LS> struct Tile {
@@ -493,15 +379,8 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
                 if (d < 4) load_link<S, R>(a.lk_out, jcb, mu, u);
                 else load_link<S, R>(a.lk_in, ncb, mu, u);
                 rebuild_row2(u);
-                if constexpr (sizeof(R) == 4) {
-                    // (re, re, im, im) per entry: broadcast operands of the packed product
-                    float4* d4 = reinterpret_cast<float4*>(sl + j * LK);
 #pragma unroll
-                    for (int e = 0; e < 9; ++e) d4[e] = make_float4(u[2 * e], u[2 * e], u[2 * e + 1], u[2 * e + 1]);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 18; ++i) sl[j * LK + i] = u[i];
-                }
+                for (int i = 0; i < 18; ++i) sl[j * LK + i] = u[i];
             }
         }
         __syncthreads();
@@ -509,56 +388,7 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
 
     // ---------------- phase 1: hop and staging --------------------------
     if (valid) {
-        if constexpr (KT::HOP && sizeof(R) == 4) {
-            // packed FP32x2 path: spinors in pair order, accumulators are
-            // pairs over the two spins of each chirality
-            float2 au[6], ad[6];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) au[i] = ad[i] = make_float2(0.f, 0.f);
-            constexpr int FS = KT::DAG ? +1 : -1;
-#pragma unroll
-            for (int mu = 0; mu < 4; ++mu) {
-#pragma unroll
-                for (int dir = 0; dir < 2; ++dir) {
-                    const unsigned nb = snb[il * 8 + dir * 4 + mu];
-                    const long ncb = (long)(nb & 0x7fffffffu);
-                    const float ph = (mu == 3 && (nb >> 31)) ? (float)a.g.tbc : 1.f;
-                    float p[24];
-                    load_raw<S, float>(a.in, a.in_nrm, ncb, s, LS, p);
-                    if constexpr (KT::PRE) {
-                        float q[12];
-                        const int sm = (s == 0) ? LS - 1 : s - 1;
-                        const float fu = (s == 0) ? -cf.mzb : cf.zb;
-                        load_half<S, float>(a.in, a.in_nrm, ncb, sm, LS, 0, q);
-#pragma unroll
-                        for (int i = 0; i < 12; ++i) p[i] = fmaf(fu, q[i], p[i]);
-                        const int sp = (s == LS - 1) ? 0 : s + 1;
-                        const float fd = (s == LS - 1) ? -cf.mzb : cf.zb;
-                        load_half<S, float>(a.in, a.in_nrm, ncb, sp, LS, 1, q);
-#pragma unroll
-                        for (int i = 0; i < 12; ++i) p[12 + i] = fmaf(fd, q[i], p[12 + i]);
-                    }
-                    const float4* lk = reinterpret_cast<const float4*>(sl + (il * 8 + dir * 4 + mu) * LK);
-                    if (dir == 0) {
-                        if (mu == 0) hop_dir2<0, FS, false>(au, ad, p, lk, ph);
-                        if (mu == 1) hop_dir2<1, FS, false>(au, ad, p, lk, ph);
-                        if (mu == 2) hop_dir2<2, FS, false>(au, ad, p, lk, ph);
-                        if (mu == 3) hop_dir2<3, FS, false>(au, ad, p, lk, ph);
-                    } else {
-                        if (mu == 0) hop_dir2<0, -FS, true>(au, ad, p, lk, ph);
-                        if (mu == 1) hop_dir2<1, -FS, true>(au, ad, p, lk, ph);
-                        if (mu == 2) hop_dir2<2, -FS, true>(au, ad, p, lk, ph);
-                        if (mu == 3) hop_dir2<3, -FS, true>(au, ad, p, lk, ph);
-                    }
-                }
-            }
-            float2* dst = reinterpret_cast<float2*>(sh + row * ST);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                dst[i] = au[i];
-                dst[6 + i] = ad[i];
-            }
-        } else if constexpr (KT::HOP) {
+        if constexpr (KT::HOP) {
             R acc[24];
 #pragma unroll
             for (int i = 0; i < 24; ++i) acc[i] = (R)0;
@@ -571,7 +401,7 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
                     const long ncb = (long)(nb & 0x7fffffffu);
                     const R ph = (mu == 3 && (nb >> 31)) ? (R)a.g.tbc : (R)1;
                     R p[24];
-                    load_raw<S, R>(a.in, a.in_nrm, ncb, s, LS, p);
+                    load_sp<S, R>(a.in, a.in_nrm, ncb, s, LS, p);
                     if constexpr (KT::PRE) {
                         // chi = psi + (c5/b5) L psi (the b5 factor is applied in phase 2)
                         R q[12];
@@ -610,7 +440,7 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
         }
         if constexpr (KT::HASY) {
             R v[24];
-            load_raw<S, R>(a.y, a.y_nrm, xcb, s, LS, v);
+            load_sp<S, R>(a.y, a.y_nrm, xcb, s, LS, v);
 #pragma unroll
             for (int i = 0; i < 24; ++i) sy[row * ST + i] = v[i];
         }
@@ -626,13 +456,12 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
         const int chi = cc >= 6 ? 1 : 0;     // 0: P+, 1: P-
         const bool shv = cf.has_shift && (chi == cf.cs);
         const int base = ci * LS;
-        const int ore = col_off<R>(cc), oim = ore + ImStep<R>::V;  // row offsets of re, im
         C2<R> v[LS];
         if constexpr (KIND == KIND_EO_MINV) {
 #pragma unroll
             for (int k = 0; k < LS; ++k) {
                 const int r = base + (chi ? LS - 1 - k : k);
-                v[k] = {sh[r * ST + ore], sh[r * ST + oim]};
+                v[k] = {sh[r * ST + 2 * cc], sh[r * ST + 2 * cc + 1]};
             }
             op_Minv<R, LS>(v, cf, shv);
             op_fwd<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
@@ -643,7 +472,7 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
 #pragma unroll
             for (int k = 0; k < LS; ++k) {
                 const int r = base + (chi ? LS - 1 - k : k);
-                v[k] = {sh[r * ST + ore], sh[r * ST + oim]};
+                v[k] = {sh[r * ST + 2 * cc], sh[r * ST + 2 * cc + 1]};
             }
             op_fwdT<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
             op_MinvT<R, LS>(v, cf, shv);
@@ -653,7 +482,7 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
 #pragma unroll
             for (int k = 0; k < LS; ++k) {
                 const int r = base + (chi ? LS - 1 - k : k);
-                v[k] = {sy[r * ST + ore], sy[r * ST + oim]};
+                v[k] = {sy[r * ST + 2 * cc], sy[r * ST + 2 * cc + 1]};
             }
             if constexpr (KIND == KIND_OE_SCHUR || KIND == KIND_FULL) op_M<R, LS>(v, cf, shv);
             if constexpr (KIND == KIND_OE_SCHUR_DAG || KIND == KIND_FULL_DAG) op_MT<R, LS>(v, cf, shv);
@@ -662,7 +491,7 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
 #pragma unroll
                 for (int k = 0; k < LS; ++k) {
                     const int r = base + (chi ? LS - 1 - k : k);
-                    w[k] = {sh[r * ST + ore], sh[r * ST + oim]};
+                    w[k] = {sh[r * ST + 2 * cc], sh[r * ST + 2 * cc + 1]};
                 }
                 if constexpr (KIND == KIND_OE_SCHUR_DAG || KIND == KIND_FULL_DAG)
                     op_fwdT<R, LS>(w, cf.b5, cf.c5, cf.m * cf.c5);
@@ -684,8 +513,8 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
 #pragma unroll
         for (int k = 0; k < LS; ++k) {
             const int r = base + (chi ? LS - 1 - k : k);
-            sh[r * ST + ore] = v[k].re;
-            sh[r * ST + oim] = v[k].im;
+            sh[r * ST + 2 * cc] = v[k].re;
+            sh[r * ST + 2 * cc + 1] = v[k].im;
         }
     }
     __syncthreads();
@@ -696,7 +525,7 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
         R v[24];
 #pragma unroll
         for (int i = 0; i < 24; ++i) v[i] = sh[row * ST + i];
-        store_raw<S, R>(a.out, a.out_nrm, xcb, s, LS, v);
+        store_sp<S, R>(a.out, a.out_nrm, xcb, s, LS, v);
         if (a.rd.fin != FIN_NONE) {
 #pragma unroll
             for (int i = 0; i < 24; ++i) nn += v[i] * v[i];
