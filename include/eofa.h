@@ -118,6 +118,8 @@ typedef struct {
     double hop_ms;       /* summed hop-kernel time (kernel_timing = 1) */
     double hop_bytes;    /* algorithmic bytes moved by the timed hop kernels */
     long kernel_launches;/* kernels this library launched during the call */
+    int precond_iters;   /* flexible-GCR steps with the learned preconditioner (precond = 1) */
+    int precond_fallbacks; /* inner solves handed to CGNR because a GCR cycle did not halve |r| */
 } eofa_solve_stats;
 
 typedef struct eofa_ctx eofa_ctx;
@@ -164,6 +166,74 @@ eofa_status eofa_solve_batched(eofa_ctx *const *ctx, int n, const void *const *r
 
 /* Release the context and all its device memory. */
 void eofa_destroy(eofa_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Learned preconditioner.  The paper preconditions only with even-odd and
+ * Cayley form; this is an additional preconditioner for the inner solver.
+ *
+ * Network: three 3^4 convolutions over the full 4D lattice, periodic in
+ * every direction, applied to each s-slice on its own (the slices are the
+ * batch); real channels 24 -> 32 -> 32 -> 24 (the spinor's 12 complex
+ * spin-colour components in the order [spin][colour][re, im]); no biases;
+ * LeakyReLU with slope 0.1 after the first two layers.  On the device the
+ * weights and activations are BF16 and the products accumulate in FP32 on
+ * the tensor cores.
+ *
+ * Weights: EOFA_NET_WEIGHTS host floats, the three layers one after another,
+ * each as W[tap][co][ci] with (ci, co) = (24, 32), (32, 32), (32, 24) and
+ * tap = ((dt*3 + dz)*3 + dy)*3 + dx for the neighbour offset
+ * (dx-1, dy-1, dz-1, dt-1):  y[x][co] = sum_tap sum_ci W[tap][co][ci] in[x+off][ci].
+ * ------------------------------------------------------------------------- */
+#define EOFA_NET_WEIGHTS 207360
+
+/* out = net(in) for nslices 4D fields of dims {X, Y, Z, T}.  in, out: device
+ * FP32 arrays [slice][t][z][y][x][24].  Allocates and frees its own device
+ * work space; synchronises stream. */
+eofa_status eofa_net_forward(const float *weights, const int dims[4], int nslices,
+                             const void *in, void *out, void *stream);
+
+/* Gradients of a loss L through the network at input `in`: given
+ * dout = dL/d(out) (device FP32, layout of out) writes dL/dW to the host
+ * array dweights (EOFA_NET_WEIGHTS floats) and, if din is not NULL,
+ * dL/d(in) to device memory.  Synchronises stream. */
+eofa_status eofa_net_backward(const float *weights, const int dims[4], int nslices,
+                              const void *in, const void *dout, float *dweights, void *din,
+                              void *stream);
+
+typedef struct {
+    int pairs;            /* (residual, error) slice pairs to train on (e.g. 2000) */
+    int snapshot_every;   /* CG iterations between snapshots of the iterate */
+    int epochs;           /* passes over the pairs */
+    int batch;            /* slices per Adam step, at most Ls/2 */
+    double lr;            /* Adam step size */
+    double solve_tol;     /* relative tolerance of the FP32 solves that make the pairs */
+} eofa_train_opts;
+
+typedef struct {
+    int pairs, steps, solves;
+    double loss_first;    /* mean relative squared error of the first step */
+    double loss_last;     /* same, last step */
+    double seconds;
+} eofa_train_stats;
+
+/* Train the network on the context's lattice.  For each source (device
+ * complex128 5D fields, H form) the inner FP32 CGNR on the Schur complement
+ * runs to solve_tol with snapshots x_k of its iterate; with the converged
+ * x*, each snapshot gives the pair (r_k = S (x* - x_k), e_k = x* - x_k)
+ * restricted to one s-slice.  Adam on the relative squared error
+ * |net(r) - e|^2 / |e|^2 over the odd sites, starting from init_weights
+ * (host; the random initial values are the caller's).  The trained weights
+ * go to weights_out (host).  Sources must be enough to give `pairs` pairs. */
+eofa_status eofa_train_preconditioner(eofa_ctx *ctx, const void *const *sources, int n_sources,
+                                      const float *init_weights, const eofa_train_opts *opts,
+                                      float *weights_out, eofa_train_stats *stats, void *stream);
+
+/* Load network weights (host FP32) into the context; eofa_solve with
+ * opts->precond = 1 then runs the inner solve as flexible GCR(4) on the
+ * Schur complement with z = net(r) as the preconditioner (FP32), falling back
+ * to CGNR when a restart cycle fails to halve the residual.  The FP64 outer
+ * defect correction and the true-residual check are unchanged. */
+eofa_status eofa_set_preconditioner(eofa_ctx *ctx, const float *weights);
 
 /* out = K in, the same result as eofa_apply, for callers that cannot call
  * cudaMalloc: for example a host framework that owns all device memory

@@ -48,7 +48,23 @@ class eofa_solve_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("inner_iters", C.c_int),
                 ("hop_launches", C.c_int), ("true_res", C.c_double), ("recur_res", C.c_double),
                 ("seconds", C.c_double), ("hop_ms", C.c_double), ("hop_bytes", C.c_double),
-                ("kernel_launches", C.c_long)]
+                ("kernel_launches", C.c_long), ("precond_iters", C.c_int), ("precond_fallbacks", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+NET_WEIGHTS = 207360
+
+
+class eofa_train_opts(C.Structure):
+    _fields_ = [("pairs", C.c_int), ("snapshot_every", C.c_int), ("epochs", C.c_int), ("batch", C.c_int),
+                ("lr", C.c_double), ("solve_tol", C.c_double)]
+
+
+class eofa_train_stats(C.Structure):
+    _fields_ = [("pairs", C.c_int), ("steps", C.c_int), ("solves", C.c_int), ("loss_first", C.c_double),
+                ("loss_last", C.c_double), ("seconds", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -56,6 +72,7 @@ class eofa_solve_stats(C.Structure):
 
 # name -> (argtypes, restype); must match include/eofa.h
 _vp = C.c_void_p
+_fp = C.POINTER(C.c_float)
 SIGNATURES = {
     "eofa_create": ([C.POINTER(eofa_params), _vp, _vp, C.POINTER(_vp)], C.c_int),
     "eofa_apply": ([_vp, _vp, _vp, _vp], C.c_int),
@@ -67,6 +84,11 @@ SIGNATURES = {
                             C.POINTER(eofa_solve_opts), C.POINTER(eofa_solve_stats), _vp], C.c_int),
     "eofa_destroy": ([_vp], None),
     "eofa_apply_noalloc": ([C.POINTER(eofa_params), _vp, _vp, _vp, _vp], C.c_int),
+    "eofa_net_forward": ([_fp, C.POINTER(C.c_int), C.c_int, _vp, _vp, _vp], C.c_int),
+    "eofa_net_backward": ([_fp, C.POINTER(C.c_int), C.c_int, _vp, _vp, _fp, _vp, _vp], C.c_int),
+    "eofa_train_preconditioner": ([_vp, C.POINTER(_vp), C.c_int, _fp, C.POINTER(eofa_train_opts), _fp,
+                                   C.POINTER(eofa_train_stats), _vp], C.c_int),
+    "eofa_set_preconditioner": ([_vp, _fp], C.c_int),
     "eofa_status_string": ([C.c_int], C.c_char_p),
     "eofa_last_error": ([_vp], C.c_char_p),
     "eofa_hop_bytes": ([_vp, C.c_int, C.c_int], C.c_double),
@@ -185,6 +207,60 @@ def eofa_apply_noalloc(params, gauge, inp, out, stream=None):
     """out = K inp without any device allocation (no context; small lattices)."""
     _check(None, lib().eofa_apply_noalloc(C.byref(params), _dptr(gauge), _dptr(inp), _dptr(out),
                                           _stream(stream)))
+
+
+def _f32ptr(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(_fp)
+
+
+def _f32dev(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("network fields must be contiguous float32 CUDA tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def eofa_net_forward(weights, dims, inp, out, stream=None):
+    """out = net(inp); inp, out: float32 CUDA tensors (S, T, Z, Y, X, 24)."""
+    w, wp = _f32ptr(weights)
+    d = (C.c_int * 4)(*[int(x) for x in dims])
+    _check(None, lib().eofa_net_forward(wp, d, int(inp.shape[0]), _f32dev(inp), _f32dev(out), _stream(stream)))
+
+
+def eofa_net_backward(weights, dims, inp, dout, din=None, stream=None):
+    """dL/dW (numpy float32, NET_WEIGHTS) and, if din is given, dL/d(inp) into din."""
+    w, wp = _f32ptr(weights)
+    d = (C.c_int * 4)(*[int(x) for x in dims])
+    dw = np.zeros(NET_WEIGHTS, dtype=np.float32)
+    _check(None, lib().eofa_net_backward(wp, d, int(inp.shape[0]), _f32dev(inp), _f32dev(dout),
+                                         dw.ctypes.data_as(_fp), _f32dev(din) if din is not None else None,
+                                         _stream(stream)))
+    return dw
+
+
+def make_train_opts(pairs=2000, snapshot_every=8, epochs=3, batch=8, lr=1e-3, solve_tol=1e-6):
+    o = eofa_train_opts()
+    o.pairs, o.snapshot_every, o.epochs, o.batch = int(pairs), int(snapshot_every), int(epochs), int(batch)
+    o.lr, o.solve_tol = float(lr), float(solve_tol)
+    return o
+
+
+def eofa_train_preconditioner(ctx, sources, init_weights, opts, stream=None):
+    """Train on the context's lattice; returns (weights numpy float32, stats)."""
+    n = len(sources)
+    sa = (C.c_void_p * n)(*[_dptr(t).value for t in sources])
+    w, wp = _f32ptr(init_weights)
+    out = np.zeros(NET_WEIGHTS, dtype=np.float32)
+    st = eofa_train_stats()
+    _check(ctx, lib().eofa_train_preconditioner(ctx, sa, n, wp, C.byref(opts), out.ctypes.data_as(_fp),
+                                                C.byref(st), _stream(stream)))
+    return out, st
+
+
+def eofa_set_preconditioner(ctx, weights):
+    w, wp = _f32ptr(weights)
+    _check(ctx, lib().eofa_set_preconditioner(ctx, wp))
 
 
 def eofa_destroy(ctx):

@@ -3,6 +3,7 @@
 // caller's canonical complex128 fields and the internal even-odd blocked
 // layout.  One thread per 5D site (xcb, s) of a half lattice.
 #include "blas.h"
+#include "learned.h"
 
 namespace eofa {
 
@@ -436,5 +437,183 @@ cudaError_t gauge_import(const double* U, const Geom& g, void* const links[4][2]
 }
 
 int blas_max_grid(long n5) { return grid_for(n5); }
+
+// ===========================================================================
+// learned preconditioner support: layout bridges and complex BLAS (FP32)
+// ===========================================================================
+
+// odd-parity FP32 field (even-odd layout) -> activations [Ls][V][32] BF16 on
+// the full lattice, zero on even sites; slice sl only when sl >= 0 (then the
+// output is one [V][32] slice), scaled by scale (or 1/sqrt(store[slot]) when
+// slot >= 0)
+__global__ void __launch_bounds__(BT) k_embed_odd(VecRef f, bf16* __restrict__ act, Geom g, int sl,
+                                                  double scale, const DevScal* sc, int slot) {
+    const long V = 2L * g.Vh;
+    const int ns = sl >= 0 ? 1 : g.Ls;
+    const long t = (long)blockIdx.x * BT + threadIdx.x;
+    if (t >= V * ns) return;
+    const int s = sl >= 0 ? sl : (int)(t / V);
+    const long lex = t % V;
+    int rem = (int)lex;
+    const int x = rem % g.X; rem /= g.X;
+    const int y = rem % g.Y; rem /= g.Y;
+    const int z = rem % g.Z;
+    const int tt = rem / g.Z;
+    bf16* dst = act + t * kCP;
+    float v[24];
+    if ((x + y + z + tt) & 1) {
+        load_sp<float, float>(f.d, f.n, lex >> 1, s, g.Ls, v);
+        float a = (float)scale;
+        if (slot >= 0) {
+            const double q = sc->store[slot];
+            a = q > 0.0 ? (float)(1.0 / sqrt(q)) : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 24; ++i) v[i] *= a;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 24; ++i) v[i] = 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < 24; i += 2)
+        *reinterpret_cast<__nv_bfloat162*>(dst + i) = __floats2bfloat162_rn(v[i], v[i + 1]);
+#pragma unroll
+    for (int i = 24; i < 32; i += 2)
+        *reinterpret_cast<__nv_bfloat162*>(dst + i) = __floats2bfloat162_rn(0.f, 0.f);
+}
+
+// network output [Ls][V][32] FP32 -> odd-parity FP32 field
+__global__ void __launch_bounds__(BT) k_extract_odd(const float* __restrict__ out32, VecRef f, Geom g) {
+    const long t = (long)blockIdx.x * BT + threadIdx.x;
+    const long n5 = (long)g.Vh * g.Ls;
+    if (t >= n5) return;
+    const long xcb = t / g.Ls;
+    const int s = (int)(t - xcb * g.Ls);
+    const long lex = lex_of(g, xcb, 1);
+    const float* src = out32 + ((long)s * 2 * g.Vh + lex) * kCP;
+    float v[24];
+#pragma unroll
+    for (int i = 0; i < 24; ++i) v[i] = src[i];
+    store_sp<float, float>(f.d, f.n, xcb, s, g.Ls, v);
+}
+
+// <a, b> = sum conj(a) b over an FP32 field: real part into rr, imaginary into ri
+__global__ void __launch_bounds__(BT) k_cdot(VecRef a, VecRef b, long n5, int Ls, Reduce rr, Reduce ri) {
+    const long t = (long)blockIdx.x * BT + threadIdx.x;
+    float re = 0.f, im = 0.f;
+    if (t < n5) {
+        const long xcb = t / Ls;
+        const int s = (int)(t - xcb * Ls);
+        float av[24], bv[24];
+        load_sp<float, float>(a.d, a.n, xcb, s, Ls, av);
+        load_sp<float, float>(b.d, b.n, xcb, s, Ls, bv);
+#pragma unroll
+        for (int i = 0; i < 24; i += 2) {
+            re += av[i] * bv[i] + av[i + 1] * bv[i + 1];
+            im += av[i] * bv[i + 1] - av[i + 1] * bv[i];
+        }
+    }
+    block_reduce_finalize<BT>(re, rr);
+    __syncthreads();
+    block_reduce_finalize<BT>(im, ri);
+}
+
+// y = a x + b y with complex a = (ar, ai) and real b (FP32 fields)
+__global__ void __launch_bounds__(BT) k_caxpby(VecRef y, VecRef x, long n5, int Ls, float ar, float ai, float b) {
+    const long t = (long)blockIdx.x * BT + threadIdx.x;
+    if (t >= n5) return;
+    const long xcb = t / Ls;
+    const int s = (int)(t - xcb * Ls);
+    float xv[24], yv[24];
+    load_sp<float, float>(x.d, x.n, xcb, s, Ls, xv);
+    load_sp<float, float>(y.d, y.n, xcb, s, Ls, yv);
+#pragma unroll
+    for (int i = 0; i < 24; i += 2) {
+        const float r = ar * xv[i] - ai * xv[i + 1] + b * yv[i];
+        const float m = ar * xv[i + 1] + ai * xv[i] + b * yv[i + 1];
+        yv[i] = r;
+        yv[i + 1] = m;
+    }
+    store_sp<float, float>(y.d, y.n, xcb, s, Ls, yv);
+}
+
+// |slice sl of an FP32 field|^2 (one s-slice of the odd sites)
+__global__ void __launch_bounds__(BT) k_slice_norm(VecRef f, long vh, int Ls, int sl, Reduce rd) {
+    const long t = (long)blockIdx.x * BT + threadIdx.x;
+    float nn = 0.f;
+    if (t < vh) {
+        float v[24];
+        load_sp<float, float>(f.d, f.n, t, sl, Ls, v);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) nn += v[i] * v[i];
+    }
+    block_reduce_finalize<BT>(nn, rd);
+}
+
+// training loss: out [B][V][32] FP32, target e [B][V][32] BF16, inverse
+// norms w[B]; on odd sites, channels < 24:  dout = 2/B w (out - e),
+// loss = 1/B sum w |out - e|^2 (reduced into rd)
+__global__ void __launch_bounds__(BT) k_loss_grad(const float* __restrict__ out, const bf16* __restrict__ e,
+                                                  const float* __restrict__ w, float* __restrict__ dout, Geom g,
+                                                  int B, Reduce rd) {
+    const long V = 2L * g.Vh;
+    const long t = (long)blockIdx.x * BT + threadIdx.x;
+    float l = 0.f;
+    if (t < V * B) {
+        const int b = (int)(t / V);
+        const long lex = t % V;
+        int rem = (int)lex;
+        const int x = rem % g.X; rem /= g.X;
+        const int y = rem % g.Y; rem /= g.Y;
+        const int z = rem % g.Z;
+        const int tt = rem / g.Z;
+        const bool odd = (x + y + z + tt) & 1;
+        const float wb = w[b];
+        for (int c = 0; c < kCP; ++c) {
+            float d = 0.f;
+            if (odd && c < 24) {
+                const float diff = out[t * kCP + c] - __bfloat162float(e[t * kCP + c]);
+                l += wb * diff * diff;
+                d = 2.f * wb * diff / (float)B;
+            }
+            dout[t * kCP + c] = d;
+        }
+        l /= (float)B;
+    }
+    block_reduce_finalize<BT>(l, rd);
+}
+
+cudaError_t embed_odd(VecRef f, bf16* act, const Geom& g, int sl, double scale, const DevScal* sc, int slot,
+                      cudaStream_t st) {
+    const long n = 2L * g.Vh * (sl >= 0 ? 1 : g.Ls);
+    k_embed_odd<<<grid_for(n), BT, 0, st>>>(f, act, g, sl, scale, sc, slot);
+    return cudaGetLastError();
+}
+
+cudaError_t extract_odd(const float* out32, VecRef f, const Geom& g, cudaStream_t st) {
+    k_extract_odd<<<grid_for((long)g.Vh * g.Ls), BT, 0, st>>>(out32, f, g);
+    return cudaGetLastError();
+}
+
+cudaError_t cdot(VecRef a, VecRef b, long n5, int Ls, Reduce rr, Reduce ri, cudaStream_t st) {
+    k_cdot<<<grid_for(n5), BT, 0, st>>>(a, b, n5, Ls, rr, ri);
+    return cudaGetLastError();
+}
+
+cudaError_t caxpby(VecRef y, VecRef x, long n5, int Ls, float ar, float ai, float b, cudaStream_t st) {
+    k_caxpby<<<grid_for(n5), BT, 0, st>>>(y, x, n5, Ls, ar, ai, b);
+    return cudaGetLastError();
+}
+
+cudaError_t slice_norm(VecRef f, long vh, int Ls, int sl, Reduce rd, cudaStream_t st) {
+    k_slice_norm<<<grid_for(vh), BT, 0, st>>>(f, vh, Ls, sl, rd);
+    return cudaGetLastError();
+}
+
+cudaError_t loss_grad(const float* out, const bf16* e, const float* w, float* dout, const Geom& g, int B, Reduce rd,
+                      cudaStream_t st) {
+    k_loss_grad<<<grid_for(2L * g.Vh * B), BT, 0, st>>>(out, e, w, dout, g, B, rd);
+    return cudaGetLastError();
+}
 
 }  // namespace eofa

@@ -41,4 +41,14 @@ cudaError_t layout_export(double* dst, VecRef src, const Geom& g, int par, int g
 cudaError_t gauge_import(const double* U, const Geom& g, void* const links[4][2], int* bad, cudaStream_t st);
 int blas_max_grid(long n5);
 
+// learned preconditioner support (FP32 odd-parity fields <-> network activations)
+cudaError_t embed_odd(VecRef f, __nv_bfloat16* act, const Geom& g, int sl, double scale, const DevScal* sc,
+                      int slot, cudaStream_t st);
+cudaError_t extract_odd(const float* out32, VecRef f, const Geom& g, cudaStream_t st);
+cudaError_t cdot(VecRef a, VecRef b, long n5, int Ls, Reduce rr, Reduce ri, cudaStream_t st);
+cudaError_t caxpby(VecRef y, VecRef x, long n5, int Ls, float ar, float ai, float b, cudaStream_t st);
+cudaError_t slice_norm(VecRef f, long vh, int Ls, int sl, Reduce rd, cudaStream_t st);
+cudaError_t loss_grad(const float* out, const __nv_bfloat16* e, const float* w, float* dout, const Geom& g, int B,
+                      Reduce rd, cudaStream_t st);
+
 }  // namespace eofa

@@ -21,6 +21,7 @@
 #include "blas.h"
 #include "dslash.cuh"
 #include "eofa.h"
+#include "learned.h"
 
 using namespace eofa;
 
@@ -58,9 +59,20 @@ struct eofa_ctx {
     double hop_bytes = 0.0;
     std::vector<double> ev_bytes;
     long launches = 0;  // kernels launched since the last reset
+    int gcr_steps = 0, gcr_fallbacks = 0;  // learned-preconditioner statistics of the current solve
     // device-driven CG loops, one per inner precision
     cudaStream_t cap = nullptr;
     cudaGraphExec_t cg_exec[4] = {};
+    // learned preconditioner: weights, activations of all Ls slices on the
+    // full lattice, flexible-GCR vectors (FP32, odd parity), second
+    // reduction buffers for complex inner products
+    bool net_ready = false;
+    NetDev net;
+    bf16* act[3] = {};
+    float* out32 = nullptr;
+    VecRef gx{}, gr{}, gz[4]{}, gw[4]{};
+    double* partials2 = nullptr;
+    unsigned* counter2 = nullptr;
 };
 
 namespace {
@@ -444,6 +456,11 @@ eofa_status run_cgnr(eofa_ctx* c, int P, double tol, int maxit, int* iters, doub
     }
 }
 
+// flexible GCR with the learned preconditioner (defined with the learned
+// preconditioner below): same contract as run_cgnr for P = FP32
+eofa_status run_fgcr(eofa_ctx* c, double tol, int maxit, int* iters, cudaStream_t st, Clock::time_point t0,
+                     long timeout_ms);
+
 double default_inner_tol(int P) {
     switch (P) {
         case EOFA_F32: return 1e-5;
@@ -478,7 +495,11 @@ eofa_status solve_begin(eofa_ctx* c, const double* rhs, const double* sol, const
     ss.P = o.inner;
     if (ss.P < 0 || ss.P > 3) return fail(c, EOFA_ERR_ARG, "opts.inner must be an eofa_prec");
     if (!(o.tol > 0.0)) return fail(c, EOFA_ERR_ARG, "opts.tol must be positive");
-    if (o.precond != 0) return fail(c, EOFA_ERR_UNSUPPORTED, "learned preconditioner not loaded");
+    if (o.precond != 0 && o.precond != 1) return fail(c, EOFA_ERR_ARG, "opts.precond must be 0 or 1");
+    if (o.precond == 1) {
+        if (!c->net_ready) return fail(c, EOFA_ERR_UNSUPPORTED, "no preconditioner: call eofa_set_preconditioner");
+        if (ss.P != EOFA_F32) return fail(c, EOFA_ERR_UNSUPPORTED, "the learned preconditioner runs with inner FP32");
+    }
     ss.maxit = o.max_iter > 0 ? o.max_iter : 100000;
     ss.maxouter = o.max_outer > 0 ? o.max_outer : 100;
     ss.H = o.rhs_form == 0 ? 1 : 0;
@@ -487,6 +508,7 @@ eofa_status solve_begin(eofa_ctx* c, const double* rhs, const double* sol, const
     if ((s = ensure_inner(c, ss.P))) return s;
     c->timing = o.kernel_timing != 0;
     c->launches = 0;
+    c->gcr_steps = c->gcr_fallbacks = 0;
     c->hop_ms = 0.0;
     c->hop_launches = 0;
     c->hop_bytes = 0.0;
@@ -599,6 +621,8 @@ eofa_status solve_end(eofa_ctx* c, double* sol, const eofa_solve_opts& o, SolveS
     S.hop_launches = c->hop_launches;
     S.hop_bytes = c->hop_bytes;
     S.kernel_launches = c->launches;
+    S.precond_iters = c->gcr_steps;
+    S.precond_fallbacks = c->gcr_fallbacks;
     eofa_status result = ss.result;
     if (result == EOFA_OK && ss.bb != 0.0 && !(S.true_res <= o.tol * 1.0000001))
         result = fail(c, EOFA_ERR_NOT_CONVERGED, "true residual above tol after the outer loop");
@@ -625,7 +649,9 @@ eofa_status solve_impl(eofa_ctx* c, const double* rhs, double* sol, const eofa_s
         CKL(blas_copy(ss.P, c->inner[ss.P].r, 0, c->ro, c->n5, Ls, 1.0, 0, red(c, FIN_NONE), st), "copy");
         int its = 0;
         double irr = 0.0;
-        eofa_status is = run_cgnr(c, ss.P, itol, ss.maxit - ss.total, &its, &irr, st, ss.t0, o.timeout_ms);
+        eofa_status is = o.precond == 1
+                             ? run_fgcr(c, itol, ss.maxit - ss.total, &its, st, ss.t0, o.timeout_ms)
+                             : run_cgnr(c, ss.P, itol, ss.maxit - ss.total, &its, &irr, st, ss.t0, o.timeout_ms);
         ss.total += its;
         ++ss.outer;
         if (is == EOFA_ERR_NONFINITE || is == EOFA_ERR_TIMEOUT || is == EOFA_ERR_CUDA) {
@@ -938,8 +964,9 @@ eofa_status eofa_solve_batched(eofa_ctx* const* ctx, int n, const void* const* r
         for (int j = 0; j < i; ++j)
             if (ctx[j] == ctx[i]) return EOFA_ERR_ARG;  // one context per system
     }
-    // kernel timing is an instrumentation of the host-driven loop: solve one by one
-    if (opts->kernel_timing || opts->inner < 0 || opts->inner > 3) {
+    // kernel timing instruments the host-driven loop, and the learned
+    // preconditioner runs flexible GCR: both solve one by one
+    if (opts->kernel_timing || opts->precond || opts->inner < 0 || opts->inner > 3) {
         eofa_status first = EOFA_OK;
         for (int i = 0; i < n; ++i) {
             eofa_status s = eofa_solve(ctx[i], rhs[i], sol[i], opts, stats ? stats + i : nullptr, stream);
@@ -1113,5 +1140,417 @@ extern "C" eofa_status eofa_apply_noalloc(const eofa_params* p, const void* gaug
     }
     for (int par = 0; par < 2; ++par)
         if (layout_export((double*)out, fout[par], g, par, 0, st) != cudaSuccess) return EOFA_ERR_CUDA;
+    return EOFA_OK;
+}
+
+// ===========================================================================
+// learned preconditioner: stateless entry points for the network itself
+// ===========================================================================
+
+namespace {
+
+struct DevBuf {
+    std::vector<void*> p;
+    ~DevBuf() {
+        for (void* q : p) cudaFree(q);
+    }
+    template <typename T>
+    cudaError_t get(T** out, size_t n) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+        if (e != cudaSuccess) return e;
+        p.push_back(q);
+        *out = static_cast<T*>(q);
+        return cudaSuccess;
+    }
+};
+
+cudaError_t net_alloc(DevBuf& B, NetDev& n) {
+    cudaError_t e = B.get(&n.Wm, (size_t)kNetWeights);
+    for (int l = 0; l < kNetLayers && e == cudaSuccess; ++l) {
+        e = B.get(&n.Wf[l], (size_t)81 * 32 * 32);
+        if (e == cudaSuccess) e = B.get(&n.Wb[l], (size_t)81 * 32 * 32);
+    }
+    return e;
+}
+
+bool conv_geom(const int dims[4], int nslices, ConvGeom* g) {
+    if (!dims || nslices <= 0) return false;
+    for (int i = 0; i < 4; ++i)
+        if (dims[i] < 1) return false;
+    const long V = (long)dims[0] * dims[1] * dims[2] * dims[3];
+    if (V * nslices > (1L << 31)) return false;
+    g->X = dims[0]; g->Y = dims[1]; g->Z = dims[2]; g->T = dims[3];
+    g->V = (int)V;
+    g->S = nslices;
+    return true;
+}
+
+}  // namespace
+
+extern "C" eofa_status eofa_net_forward(const float* weights, const int dims[4], int nslices, const void* in,
+                                        void* out, void* stream) {
+    ConvGeom g;
+    if (!weights || !in || !out || !conv_geom(dims, nslices, &g)) return EOFA_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long rows = (long)g.V * g.S;
+    DevBuf B;
+    NetDev n;
+    bf16 *a0, *a1, *a2;
+    float* o32;
+    cudaError_t e = net_alloc(B, n);
+    if (e == cudaSuccess) e = B.get(&a0, rows * kCP);
+    if (e == cudaSuccess) e = B.get(&a1, rows * kCP);
+    if (e == cudaSuccess) e = B.get(&a2, rows * kCP);
+    if (e == cudaSuccess) e = B.get(&o32, rows * kCP);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(n.Wm, weights, sizeof(float) * kNetWeights, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = net_convert(n, st);
+    if (e == cudaSuccess) e = pack_act((const float*)in, a0, rows, st);
+    if (e == cudaSuccess) e = net_forward(n, g, a0, a1, a2, o32, st);
+    if (e == cudaSuccess) e = unpack_out(o32, (float*)out, rows, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? EOFA_ERR_OOM : EOFA_ERR_CUDA;
+    return EOFA_OK;
+}
+
+extern "C" eofa_status eofa_net_backward(const float* weights, const int dims[4], int nslices, const void* in,
+                                         const void* dout, float* dweights, void* din, void* stream) {
+    ConvGeom g;
+    if (!weights || !in || !dout || !dweights || !conv_geom(dims, nslices, &g)) return EOFA_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long rows = (long)g.V * g.S;
+    DevBuf B;
+    NetDev n;
+    bf16 *a0, *a1, *a2, *dob, *d1, *d2;
+    float *o32, *dout32, *dW, *din32 = nullptr;
+    cudaError_t e = net_alloc(B, n);
+    bf16** bufs[] = {&a0, &a1, &a2, &dob, &d1, &d2};
+    for (auto b : bufs)
+        if (e == cudaSuccess) e = B.get(b, rows * kCP);
+    if (e == cudaSuccess) e = B.get(&o32, rows * kCP);
+    if (e == cudaSuccess) e = B.get(&dout32, rows * kCP);
+    if (e == cudaSuccess) e = B.get(&dW, (size_t)kNetWeights);
+    if (e == cudaSuccess && din) e = B.get(&din32, rows * kCP);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(n.Wm, weights, sizeof(float) * kNetWeights, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dW, 0, sizeof(float) * kNetWeights, st);
+    if (e == cudaSuccess) e = net_convert(n, st);
+    if (e == cudaSuccess) e = pack_act((const float*)in, a0, rows, st);
+    if (e == cudaSuccess) e = net_forward(n, g, a0, a1, a2, o32, st);
+    if (e == cudaSuccess) e = pad_f32((const float*)dout, dout32, rows, st);
+    if (e == cudaSuccess) e = net_backward(n, g, a0, a1, a2, dout32, dW, din32, dob, d1, d2, st);
+    if (e == cudaSuccess && din) e = unpack_out(din32, (float*)din, rows, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dweights, dW, sizeof(float) * kNetWeights, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? EOFA_ERR_OOM : EOFA_ERR_CUDA;
+    return EOFA_OK;
+}
+
+// ===========================================================================
+// learned preconditioner inside the solver
+// ===========================================================================
+namespace {
+
+constexpr int kGcrM = 4;  // flexible GCR restart length
+
+Reduce red2(eofa_ctx* c, int fin, int slot) {
+    Reduce r;
+    r.partials = c->partials2;
+    r.counter = c->counter2;
+    r.scal = c->scal;
+    r.fin = fin;
+    r.slot = slot;
+    return r;
+}
+
+eofa_status ensure_learned(eofa_ctx* c) {
+    if (c->act[0]) return EOFA_OK;
+    const long rows = 2L * c->g.Vh * c->g.Ls;
+    eofa_status s;
+    void* p = nullptr;
+    for (int i = 0; i < 3; ++i) {
+        if ((s = dalloc(c, &p, sizeof(bf16) * rows * kCP))) return s;
+        c->act[i] = (bf16*)p;
+    }
+    if ((s = dalloc(c, &p, sizeof(float) * rows * kCP))) return s;
+    c->out32 = (float*)p;
+    if ((s = vec_alloc(c, EOFA_F32, &c->gx)) || (s = vec_alloc(c, EOFA_F32, &c->gr))) return s;
+    for (int k = 0; k < kGcrM; ++k)
+        if ((s = vec_alloc(c, EOFA_F32, &c->gz[k])) || (s = vec_alloc(c, EOFA_F32, &c->gw[k]))) return s;
+    const int maxgrid = std::max(blas_max_grid(c->n5), c->g.Vh / 8 + 2);
+    if ((s = dalloc(c, &p, sizeof(double) * maxgrid))) return s;
+    c->partials2 = (double*)p;
+    if ((s = dalloc(c, &p, 256))) return s;
+    c->counter2 = (unsigned*)p;
+    CK(cudaMemset(c->counter2, 0, 256), "memset");
+    if ((s = dalloc(c, &p, sizeof(float) * kNetWeights))) return s;
+    c->net.Wm = (float*)p;
+    for (int l = 0; l < kNetLayers; ++l) {
+        if ((s = dalloc(c, &p, sizeof(bf16) * 81 * 32 * 32))) return s;
+        c->net.Wf[l] = (bf16*)p;
+        if ((s = dalloc(c, &p, sizeof(bf16) * 81 * 32 * 32))) return s;
+        c->net.Wb[l] = (bf16*)p;
+    }
+    return EOFA_OK;
+}
+
+ConvGeom conv_geom_of(const eofa_ctx* c, int slices) {
+    ConvGeom cg;
+    cg.X = c->g.X; cg.Y = c->g.Y; cg.Z = c->g.Z; cg.T = c->g.T;
+    cg.V = 2 * c->g.Vh;
+    cg.S = slices;
+    return cg;
+}
+
+// z = net(r) for every s-slice of an odd-parity FP32 field
+eofa_status net_apply(eofa_ctx* c, VecRef in, VecRef out, cudaStream_t st) {
+    CKL(embed_odd(in, c->act[0], c->g, -1, 1.0, c->scal, -1, st), "embed");
+    CK(net_forward(c->net, conv_geom_of(c, c->g.Ls), c->act[0], c->act[1], c->act[2], c->out32, st), "net");
+    c->launches += 3;
+    CKL(extract_odd(c->out32, out, c->g, st), "extract");
+    return EOFA_OK;
+}
+
+// <a, b> read back to the host (slots 4 and 5 are free during inner solves)
+eofa_status dot_host(eofa_ctx* c, VecRef a, VecRef b, double* re, double* im, cudaStream_t st) {
+    CKL(cdot(a, b, c->n5, c->g.Ls, red(c, FIN_STORE, 4), red2(c, FIN_STORE, 5), st), "cdot");
+    eofa_status s;
+    if ((s = read_scal(c, st))) return s;
+    *re = c->h_scal->store[4];
+    *im = c->h_scal->store[5];
+    return EOFA_OK;
+}
+
+// Flexible GCR(kGcrM) on the Schur complement S in FP32 with the learned
+// preconditioner: z_k = net(r), w_k = S z_k orthonormalised against the
+// cycle's earlier w_j (modified Gram-Schmidt, the same combination applied
+// to z_k), x += <w_k, r> z_k, r -= <w_k, r> w_k.  A restart cycle that does
+// not halve |r| hands the rest of the solve to CGNR (the plain method
+// stays the fallback).  Unit source in inner[F32].r, result in inner[F32].x.
+eofa_status run_fgcr(eofa_ctx* c, double tol, int maxit, int* iters, cudaStream_t st, Clock::time_point t0,
+                     long timeout_ms) {
+    Inner& in = c->inner[EOFA_F32];
+    const long n5 = c->n5;
+    const int Ls = c->g.Ls;
+    const VecRef none{};
+    eofa_status s;
+    if ((s = ensure_learned(c))) return s;
+    CKL(blas_copy(EOFA_F32, c->gr, EOFA_F32, in.r, n5, Ls, 1.0, -1, red(c, FIN_NONE), st), "copy");
+    CKL(blas_zero(EOFA_F32, c->gx, n5, Ls, st), "zero");
+    double rr, im;
+    if ((s = dot_host(c, c->gr, c->gr, &rr, &im, st))) return s;
+    *iters = 0;
+    auto finish = [&](eofa_status r) -> eofa_status {
+        CKL(blas_copy(EOFA_F32, in.x, EOFA_F32, c->gx, n5, Ls, 1.0, -1, red(c, FIN_NONE), st), "copy");
+        return r;
+    };
+    for (;;) {
+        const double cycle_rr = rr;
+        for (int k = 0; k < kGcrM; ++k) {
+            if ((s = net_apply(c, c->gr, c->gz[k], st))) return s;
+            if ((s = hop(c, EOFA_F32, KIND_EO_MINV, 0, c->gz[k], none, in.t, red(c, FIN_NONE), nullptr, st)))
+                return s;
+            if ((s = hop(c, EOFA_F32, KIND_OE_SCHUR, 1, in.t, c->gz[k], c->gw[k], red(c, FIN_NONE), nullptr, st)))
+                return s;
+            double br, bi;
+            for (int j = 0; j < k; ++j) {
+                if ((s = dot_host(c, c->gw[j], c->gw[k], &br, &bi, st))) return s;
+                CKL(caxpby(c->gw[k], c->gw[j], n5, Ls, (float)-br, (float)-bi, 1.f, st), "caxpby");
+                CKL(caxpby(c->gz[k], c->gz[j], n5, Ls, (float)-br, (float)-bi, 1.f, st), "caxpby");
+            }
+            double nn;
+            if ((s = dot_host(c, c->gw[k], c->gw[k], &nn, &bi, st))) return s;
+            if (!(nn > 0.0) || !std::isfinite(nn)) break;  // no new direction: fall back below
+            const float sc = (float)(1.0 / std::sqrt(nn));
+            CKL(caxpby(c->gw[k], c->gw[k], n5, Ls, 0.f, 0.f, sc, st), "scale");
+            CKL(caxpby(c->gz[k], c->gz[k], n5, Ls, 0.f, 0.f, sc, st), "scale");
+            double ar, ai;
+            if ((s = dot_host(c, c->gw[k], c->gr, &ar, &ai, st))) return s;
+            CKL(caxpby(c->gx, c->gz[k], n5, Ls, (float)ar, (float)ai, 1.f, st), "caxpby");
+            CKL(caxpby(c->gr, c->gw[k], n5, Ls, (float)-ar, (float)-ai, 1.f, st), "caxpby");
+            if ((s = dot_host(c, c->gr, c->gr, &rr, &im, st))) return s;
+            ++*iters;
+            ++c->gcr_steps;
+            if (!std::isfinite(rr)) return fail(c, EOFA_ERR_NONFINITE, "non-finite residual in flexible GCR");
+            if (rr <= tol * tol) return finish(EOFA_OK);
+            if (*iters >= maxit) return finish(EOFA_ERR_NOT_CONVERGED);
+            if (timeout_ms > 0 && since(t0) * 1e3 > (double)timeout_ms)
+                return fail(c, EOFA_ERR_TIMEOUT, "solve exceeded timeout_ms");
+        }
+        if (rr > 0.25 * cycle_rr) {
+            // the cycle did not halve |r|: CGNR solves S e = r / |r|, x += |r| e
+            ++c->gcr_fallbacks;
+            const double rn = std::sqrt(rr);
+            CKL(blas_copy(EOFA_F32, in.r, EOFA_F32, c->gr, n5, Ls, 1.0 / rn, -1, red(c, FIN_NONE), st), "copy");
+            int cits = 0;
+            double crr = 0.0;
+            eofa_status cs = run_cgnr(c, EOFA_F32, tol / rn, maxit - *iters, &cits, &crr, st, t0, timeout_ms);
+            *iters += cits;
+            CKL(caxpby(in.x, c->gx, n5, Ls, 1.f, 0.f, (float)rn, st), "caxpby");
+            return cs;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" eofa_status eofa_set_preconditioner(eofa_ctx* ctx, const float* weights) {
+    if (!ctx || !weights) return EOFA_ERR_ARG;
+    eofa_ctx* c = ctx;
+    eofa_status s;
+    if ((s = ensure_learned(c))) return s;
+    CK(cudaMemcpy(c->net.Wm, weights, sizeof(float) * kNetWeights, cudaMemcpyHostToDevice), "upload weights");
+    CK(net_convert(c->net, nullptr), "convert weights");
+    CK(cudaDeviceSynchronize(), "sync");
+    c->net_ready = true;
+    return EOFA_OK;
+}
+
+extern "C" eofa_status eofa_train_preconditioner(eofa_ctx* ctx, const void* const* sources, int n_sources,
+                                                 const float* init_weights, const eofa_train_opts* opts,
+                                                 float* weights_out, eofa_train_stats* stats, void* stream) {
+    if (!ctx || !sources || n_sources <= 0 || !init_weights || !opts || !weights_out) return EOFA_ERR_ARG;
+    if (opts->pairs <= 0 || opts->snapshot_every <= 0 || opts->epochs <= 0 || opts->batch <= 0 || !(opts->lr > 0.0) ||
+        !(opts->solve_tol > 0.0))
+        return EOFA_ERR_ARG;
+    eofa_ctx* c = ctx;
+    cudaStream_t st = (cudaStream_t)stream;
+    const auto t0 = Clock::now();
+    eofa_status s;
+    if ((s = ensure_inner(c, EOFA_F32)) || (s = ensure_learned(c))) return s;
+    CK(cudaMemcpyAsync(c->net.Wm, init_weights, sizeof(float) * kNetWeights, cudaMemcpyHostToDevice, st), "upload");
+    CK(net_convert(c->net, st), "convert");
+    const Geom& g = c->g;
+    const long V = 2L * g.Vh, n5 = c->n5;
+    const int Ls = g.Ls, B = opts->batch;
+    const int P = opts->pairs;
+    // the loss reduction shares the context's reduction buffers, sized for
+    // one half-lattice 5D field: a batch holds at most Ls/2 full-lattice slices
+    if (2L * B > Ls) return fail(c, EOFA_ERR_ARG, "train batch must be at most Ls/2");
+    constexpr int kMaxSnap = 64;
+    DevBuf D;
+    bf16 *pr, *pe, *a0, *a1, *a2, *et, *dob, *d1, *d2;
+    float *o32, *dout, *dW, *am, *av, *wdev;
+    cudaError_t e = D.get(&pr, (size_t)P * V * kCP);
+    if (e == cudaSuccess) e = D.get(&pe, (size_t)P * V * kCP);
+    bf16** bb[] = {&a0, &a1, &a2, &et, &dob, &d1, &d2};
+    for (auto b : bb)
+        if (e == cudaSuccess) e = D.get(b, (size_t)B * V * kCP);
+    if (e == cudaSuccess) e = D.get(&o32, (size_t)B * V * kCP);
+    if (e == cudaSuccess) e = D.get(&dout, (size_t)B * V * kCP);
+    if (e == cudaSuccess) e = D.get(&dW, (size_t)kNetWeights);
+    if (e == cudaSuccess) e = D.get(&am, (size_t)kNetWeights);
+    if (e == cudaSuccess) e = D.get(&av, (size_t)kNetWeights);
+    if (e == cudaSuccess) e = D.get(&wdev, (size_t)B);
+    std::vector<VecRef> snap(kMaxSnap);
+    VecRef et5{}, rt5{};
+    for (int i = 0; i < kMaxSnap && e == cudaSuccess; ++i) e = D.get((float**)&snap[i].d, (size_t)n5 * 24);
+    if (e == cudaSuccess) e = D.get((float**)&et5.d, (size_t)n5 * 24);
+    if (e == cudaSuccess) e = D.get((float**)&rt5.d, (size_t)n5 * 24);
+    if (e == cudaSuccess) e = cudaMemsetAsync(am, 0, sizeof(float) * kNetWeights, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(av, 0, sizeof(float) * kNetWeights, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "training buffers");
+
+    // ---- pairs from the solver's own iterates ----
+    Inner& in = c->inner[EOFA_F32];
+    const VecRef none{};
+    std::vector<float> pw(P, 1.f);
+    int have = 0, solves = 0;
+    for (int j = 0; j < n_sources && have < P; ++j) {
+        SolveState ss;
+        eofa_solve_opts o;
+        std::memset(&o, 0, sizeof(o));
+        o.tol = 1e-10;
+        o.inner = EOFA_F32;
+        if ((s = solve_begin(c, (const double*)sources[j], (const double*)sources[j], o, ss, st))) return s;
+        CK(cudaStreamSynchronize(st), "sync");
+        if (c->h_scal->store[1] + c->h_scal->store[2] == 0.0) continue;
+        if ((s = outer_residual(c, st))) return s;
+        CKL(blas_copy(EOFA_F32, in.r, 0, c->ro, n5, Ls, 1.0, 0, red(c, FIN_NONE), st), "copy");
+        const double tol = opts->solve_tol;
+        CKL(scal_init(c->scal, tol * tol, 100000, 0ull, st), "scal_init");
+        CKL(blas_zero(EOFA_F32, in.x, n5, Ls, st), "zero");
+        if ((s = hop(c, EOFA_F32, KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), nullptr, st))) return s;
+        if ((s = hop(c, EOFA_F32, KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_ZZ), nullptr, st))) return s;
+        CKL(blas_copy(EOFA_F32, in.p, EOFA_F32, in.z, n5, Ls, 1.0, -1, red(c, FIN_NONE), st), "copy");
+        int ns = 1;  // snapshot 0 is the zero start vector
+        CK(cudaMemsetAsync(snap[0].d, 0, sizeof(float) * n5 * 24, st), "memset");
+        for (;;) {
+            for (int i = 0; i < opts->snapshot_every; ++i)
+                if ((s = cg_iteration(c, EOFA_F32, st, false))) return s;
+            if ((s = read_scal(c, st))) return s;
+            if (c->h_scal->nonfinite) return fail(c, EOFA_ERR_NONFINITE, "training solve");
+            if (c->h_scal->done || c->h_scal->iters >= 100000) break;
+            if (ns < kMaxSnap)
+                CKL(blas_copy(EOFA_F32, snap[ns++], EOFA_F32, in.x, n5, Ls, 1.0, -1, red(c, FIN_NONE), st), "snap");
+        }
+        ++solves;
+        for (int i = 0; i < ns && have < P; ++i) {
+            // e = x* - x_k, r = S e
+            CKL(blas_copy(EOFA_F32, et5, EOFA_F32, in.x, n5, Ls, 1.0, -1, red(c, FIN_NONE), st), "copy");
+            CKL(caxpby(et5, snap[i], n5, Ls, -1.f, 0.f, 1.f, st), "caxpby");
+            if ((s = hop(c, EOFA_F32, KIND_EO_MINV, 0, et5, none, in.t, red(c, FIN_NONE), nullptr, st))) return s;
+            if ((s = hop(c, EOFA_F32, KIND_OE_SCHUR, 1, in.t, et5, rt5, red(c, FIN_NONE), nullptr, st))) return s;
+            const int sl = have % Ls;
+            CKL(slice_norm(rt5, g.Vh, Ls, sl, red(c, FIN_STORE, 4), st), "norm");
+            CKL(slice_norm(et5, g.Vh, Ls, sl, red(c, FIN_STORE, 5), st), "norm");
+            if ((s = read_scal(c, st))) return s;
+            const double nr = c->h_scal->store[4], ne = c->h_scal->store[5];
+            if (!(nr > 0.0) || !(ne > 0.0)) continue;
+            const double sc = 1.0 / std::sqrt(nr);
+            CKL(embed_odd(rt5, pr + (size_t)have * V * kCP, g, sl, sc, c->scal, -1, st), "embed");
+            CKL(embed_odd(et5, pe + (size_t)have * V * kCP, g, sl, sc, c->scal, -1, st), "embed");
+            pw[have] = (float)(nr / ne);
+            ++have;
+        }
+    }
+    if (have == 0) return fail(c, EOFA_ERR_ARG, "no training pairs (zero sources?)");
+
+    // ---- Adam on the relative squared error ----
+    std::vector<int> perm(have);
+    for (int i = 0; i < have; ++i) perm[i] = i;
+    unsigned long long lcg = 0x9e3779b97f4a7c15ull;  // fixed-seed shuffle of the pair order
+    for (int i = have - 1; i > 0; --i) {
+        lcg = lcg * 6364136223846793005ull + 1442695040888963407ull;
+        const int k = (int)((lcg >> 33) % (unsigned long long)(i + 1));
+        std::swap(perm[i], perm[k]);
+    }
+    const int steps = std::max(1, (int)((long)opts->epochs * have / B));
+    const ConvGeom cgB = conv_geom_of(c, B);
+    std::vector<float> hw(B);
+    double loss_first = 0.0, loss_last = 0.0;
+    for (int step = 0; step < steps; ++step) {
+        for (int b = 0; b < B; ++b) {
+            const int p = perm[((long)step * B + b) % have];
+            CK(cudaMemcpyAsync(a0 + (size_t)b * V * kCP, pr + (size_t)p * V * kCP, sizeof(bf16) * V * kCP,
+                               cudaMemcpyDeviceToDevice, st), "batch");
+            CK(cudaMemcpyAsync(et + (size_t)b * V * kCP, pe + (size_t)p * V * kCP, sizeof(bf16) * V * kCP,
+                               cudaMemcpyDeviceToDevice, st), "batch");
+            hw[b] = pw[p];
+        }
+        CK(cudaMemcpyAsync(wdev, hw.data(), sizeof(float) * B, cudaMemcpyHostToDevice, st), "weights");
+        CK(net_forward(c->net, cgB, a0, a1, a2, o32, st), "forward");
+        Geom gB = g;  // loss over B slices of the full lattice
+        CK(loss_grad(o32, et, wdev, dout, gB, B, red(c, FIN_STORE, 4), st), "loss");
+        CK(cudaMemsetAsync(dW, 0, sizeof(float) * kNetWeights, st), "memset");
+        CK(net_backward(c->net, cgB, a0, a1, a2, dout, dW, nullptr, dob, d1, d2, st), "backward");
+        CK(adam_step(c->net.Wm, dW, am, av, kNetWeights, (float)opts->lr, 0.9f, 0.999f, 1e-8f, step + 1, st), "adam");
+        CK(net_convert(c->net, st), "convert");
+        if (step == 0 || step == steps - 1) {
+            if ((s = read_scal(c, st))) return s;
+            (step == 0 ? loss_first : loss_last) = c->h_scal->store[4];
+            if (step == 0) loss_last = loss_first;
+        }
+    }
+    CK(cudaMemcpyAsync(weights_out, c->net.Wm, sizeof(float) * kNetWeights, cudaMemcpyDeviceToHost, st), "download");
+    CK(cudaStreamSynchronize(st), "sync");
+    c->net_ready = true;
+    if (stats) {
+        stats->pairs = have;
+        stats->steps = steps;
+        stats->solves = solves;
+        stats->loss_first = loss_first;
+        stats->loss_last = loss_last;
+        stats->seconds = since(t0);
+    }
     return EOFA_OK;
 }

@@ -48,7 +48,7 @@ def test_struct_layouts():
     # sizes implied by include/eofa.h on LP64
     assert C.sizeof(B.eofa_params) == 4 * 4 + 4 + 4 + 7 * 8 + 4 + 4
     assert C.sizeof(B.eofa_solve_opts) == 8 + 4 + 4 + 8 + 6 * 4 + 8
-    assert C.sizeof(B.eofa_solve_stats) == 4 * 4 + 5 * 8 + 8
+    assert C.sizeof(B.eofa_solve_stats) == 4 * 4 + 5 * 8 + 8 + 2 * 4
 
 
 def test_status_strings(libeofa):
