@@ -31,6 +31,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -143,6 +145,105 @@ def oracle_sample(iters_per_sample, samples=1):
         times.append((time.perf_counter() - t0) / max(st.iters, 1))
     per_iter = statistics.median(times)
     return per_iter, n_iter, oracle.num_threads()
+
+
+def _timed(torch, fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, out
+
+
+def run_batched(B, I, torch, dev):
+    """16 right-hand sides over uneven lattices -- 8 systems on 16^4 Ls=16
+    (gauge seed 1) and 8 on 12^3x24 Ls=12 (gauge seed 2), links
+    exp(i 0.5 H) -- in one eofa_solve_batched call (FP32 inner, FP64
+    correction, one graph with a device-driven loop), against the same 16
+    solves one after another."""
+    act = dict(WORKLOAD["action"])
+    groups = [((16, 16, 16, 16), 16, 1), ((12, 12, 12, 24), 12, 2)]
+    solvers, rhs = [], []
+    k = 0
+    for dims, Ls, gseed in groups:
+        U = torch.from_numpy(I.gauge_field(dims, 0.5, gseed)).to(dev)
+        for _ in range(8):
+            solvers.append(B.Solver(U, dims, Ls, **act))
+            rhs.append(torch.from_numpy(I.gaussian_fermion(dims, Ls, 1001 + k)).to(dev))
+            k += 1
+        del U
+    sols = [torch.empty_like(r) for r in rhs]
+    opts = B.make_opts(tol=TOL, inner="f32")
+    ctxs = [s.ctx for s in solvers]
+    B.eofa_solve_batched(ctxs, rhs, sols, opts)  # warm-up
+    t_b, st = _timed(torch, lambda: B.eofa_solve_batched(ctxs, rhs, sols, opts))
+    t_s, _ = _timed(torch, lambda: [s.solve(r, out=o, tol=TOL, inner="f32") for s, r, o in zip(solvers, rhs, sols)])
+    res = {"systems": len(solvers), "s_batched": t_b, "s_one_by_one": t_s, "speedup": t_s / t_b,
+           "max_true_res": max(x.true_res for x in st), "inner_iters": [x.inner_iters for x in st],
+           "status": [x.status for x in st]}
+    for s in solvers:
+        s.close()
+    return res
+
+
+def run_multi_rhs(B, I, torch, dev):
+    """24^3x64 Ls=12, m1 = m3 = 0.0362, links exp(i 0.7 H): four right-hand
+    sides with FP16 and BF16 (and FP32) inner storage, FP64 correction."""
+    dims, Ls = (24, 24, 24, 64), 12
+    act = dict(WORKLOAD["action"], m1=0.0362, m3=0.0362)
+    U = torch.from_numpy(I.gauge_field(dims, 0.7, 1)).to(dev)
+    s = B.Solver(U, dims, Ls, **act)
+    del U
+    out = {}
+    rhs = [torch.from_numpy(I.gaussian_fermion(dims, Ls, 1001 + i)).to(dev) for i in range(4)]
+    sol = torch.empty_like(rhs[0])
+    for inner in ["f16", "bf16", "f32"]:
+        s.solve(rhs[0], out=sol, tol=TOL, inner=inner)  # warm-up (allocation, graph)
+        times, its, resid = [], [], []
+        for r in rhs:
+            dt, (_, st) = _timed(torch, lambda: s.solve(r, out=sol, tol=TOL, inner=inner))
+            times.append(dt)
+            its.append(st.inner_iters)
+            resid.append(st.true_res)
+        out[inner] = {"s_per_solve": statistics.mean(times), "inner_iters": its, "max_true_res": max(resid)}
+    s.close()
+    return out
+
+
+def run_learned(B, I, torch, dev):
+    """Learned preconditioner: trained on 2000 (residual, error) pairs from
+    16^3x32 Ls=16 solves (gauge seed 3), used in flexible GCR at 32^3x64
+    Ls=12 (FP32 inner, FP64 correction to 1e-10), against plain CGNR and the
+    untrained network."""
+    act = dict(WORKLOAD["action"])
+    rng = np.random.default_rng(17)
+    w0 = np.concatenate([rng.standard_normal(81 * co * ci) * np.sqrt(2.0 / (81 * ci))
+                         for ci, co in [(24, 32), (32, 32), (32, 24)]]).astype(np.float32)
+    dims_t, Ls_t = (16, 16, 16, 32), 16
+    Ut = torch.from_numpy(I.gauge_field(dims_t, 0.5, 3)).to(dev)
+    st_ = B.Solver(Ut, dims_t, Ls_t, **act)
+    srcs = [torch.from_numpy(I.gaussian_fermion(dims_t, Ls_t, 5000 + i)).to(dev) for i in range(40)]
+    opts = B.make_train_opts(pairs=2000, snapshot_every=8, epochs=3, batch=8, lr=1e-3, solve_tol=1e-6)
+    t_train, (w, tst) = _timed(torch, lambda: B.eofa_train_preconditioner(st_.ctx, srcs, w0, opts))
+    st_.close()
+    del srcs, Ut
+    dims, Ls = (32, 32, 32, 64), 12
+    U = torch.from_numpy(I.gauge_field(dims, 0.5, 3)).to(dev)
+    s = B.Solver(U, dims, Ls, **act)
+    del U
+    rhs = torch.from_numpy(I.gaussian_fermion(dims, Ls, 1001)).to(dev)
+    sol = torch.empty_like(rhs)
+    res = {"train": dict(tst.as_dict(), wall_s=t_train)}
+    s.solve(rhs, out=sol, tol=TOL, inner="f32")
+    dt, (_, st) = _timed(torch, lambda: s.solve(rhs, out=sol, tol=TOL, inner="f32"))
+    res["cgnr"] = {"s": dt, "inner_iters": st.inner_iters, "true_res": st.true_res}
+    for name, weights in [("trained", w), ("untrained", w0)]:
+        B.eofa_set_preconditioner(s.ctx, weights)
+        dt, (_, st) = _timed(torch, lambda: s.solve(rhs, out=sol, tol=TOL, inner="f32", precond=1))
+        res[name] = {"s": dt, "inner_iters": st.inner_iters, "gcr_steps": st.precond_iters,
+                     "fallbacks": st.precond_fallbacks, "true_res": st.true_res}
+    s.close()
+    return res
 
 
 def run_reference(args):
@@ -282,6 +383,14 @@ def run_ours(args):
                             "inner_iters": st.inner_iters, "status": st.status,
                             "hop_GBps": st.hop_bytes / (st.hop_ms * 1e-3) / 1e9 if st.hop_ms else None}
 
+    workloads = {}
+    if rank == 0 and not args.quick:
+        solver.close()
+        workloads["batched_16rhs_uneven"] = run_batched(B, I, torch, dev)
+        workloads["24^3x64_Ls12_4rhs"] = run_multi_rhs(B, I, torch, dev)
+        if args.learned:
+            workloads["learned_32^3x64_Ls12"] = run_learned(B, I, torch, dev)
+
     if rank != 0:
         return
     main = stats[-1]
@@ -323,9 +432,11 @@ def run_ours(args):
                   "inner_iters": main["inner_iters"], "kernel_launches_per_solve": launches},
         "other_precisions": extra,
         "speedup_vs_fp64": (f64 / value) if f64 and ws == 1 else None,
+        "other_workloads": workloads,
     }
     print(json.dumps(line))
-    solver.close()
+    if args.quick:
+        solver.close()
 
 
 def main():
@@ -338,6 +449,8 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=8, help="oracle iterations per CPU sample")
     ap.add_argument("--quick", action="store_true", help="skip the other-precision solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--learned", action="store_true",
+                    help="also train the learned preconditioner and time it at 32^3x64 Ls=12 (minutes)")
     ap.add_argument("--profile", action="store_true",
                     help="one solve capped at 16 inner iterations, nothing else (for ncu captures)")
     args = ap.parse_args()
