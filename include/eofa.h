@@ -270,6 +270,13 @@ const char *eofa_last_error(const eofa_ctx *ctx);
  * over Ls, plus 24 reals of the local vector when the kernel reads one. */
 double eofa_hop_bytes(const eofa_ctx *ctx, int prec, int with_local);
 
+/* 4D sites per CTA that the library's autotuner chose for hop kernel `kind`
+ * of the inner solver (0: S step 1, 1: S step 2, 2: S^dag step 1, 3: S^dag
+ * step 2) in precision prec; the default tile if that precision has not been
+ * used by a solve yet.  Block and tile shapes are timed on the context's own
+ * buffers at its first solve in a precision and cached per lattice shape. */
+int eofa_tile_sites(const eofa_ctx *ctx, int prec, int kind);
+
 #ifdef __cplusplus
 }
 #endif

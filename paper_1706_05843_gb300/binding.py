@@ -92,6 +92,7 @@ SIGNATURES = {
     "eofa_status_string": ([C.c_int], C.c_char_p),
     "eofa_last_error": ([_vp], C.c_char_p),
     "eofa_hop_bytes": ([_vp, C.c_int, C.c_int], C.c_double),
+    "eofa_tile_sites": ([_vp, C.c_int, C.c_int], C.c_int),
 }
 
 _lib = None

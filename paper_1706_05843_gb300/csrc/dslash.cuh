@@ -54,7 +54,7 @@ template <int K> struct KindTraits {
 struct HopArgs {
     Geom g;
     int out_par;
-    int pad;
+    int tile_var;                            // CTA tile variant (autotuner)
     const void* in;  const float* in_nrm;    // hop input, parity 1 - out_par
     const void* y;   const float* y_nrm;     // site-local input, parity out_par
     void* out;       float* out_nrm;         // output, parity out_par
@@ -317,18 +317,33 @@ template <typename R> struct LinkStride;
 template <> struct LinkStride<float> { static constexpr int V = 20; };
 template <> struct LinkStride<double> { static constexpr int V = 18; };
 
-template <int LS> struct Tile {
-    static constexpr int NS = (LS >= 16) ? 8 : (LS == 12 ? 16 : 128 / LS);
+// CTA tile: NS 4D sites x Ls slices, one thread per 5D site.  Variant 0 is
+// the default; variant 1 (twice the sites, or half for Ls = 12) is the
+// alternative the autotuner times against it for the inner-solver kinds.
+template <int LS, int VAR = 0> struct Tile {
+    static constexpr int NS0 = (LS >= 16) ? 8 : (LS == 12 ? 16 : 128 / LS);
+    static constexpr int NS = VAR == 0 ? NS0 : (LS == 12 ? NS0 / 2 : NS0 * 2);
     static constexpr int NT = NS * LS;
 };
 
-template <typename S, int LS, int KIND>
-__global__ void __launch_bounds__(Tile<LS>::NT)
+// sites per CTA of a tile variant (for reports)
+inline int tile_sites(int Ls, int var) {
+    switch (Ls) {
+        case 4: return var ? Tile<4, 1>::NS : Tile<4, 0>::NS;
+        case 8: return var ? Tile<8, 1>::NS : Tile<8, 0>::NS;
+        case 12: return var ? Tile<12, 1>::NS : Tile<12, 0>::NS;
+        case 16: return var ? Tile<16, 1>::NS : Tile<16, 0>::NS;
+        default: return 0;
+    }
+}
+
+template <typename S, int LS, int KIND, int VAR = 0>
+__global__ void __launch_bounds__(Tile<LS, VAR>::NT)
 hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
     typedef typename Traits<S>::R R;
     typedef KindTraits<KIND> KT;
-    constexpr int NS = Tile<LS>::NS;
-    constexpr int NT = Tile<LS>::NT;
+    constexpr int NS = Tile<LS, VAR>::NS;
+    constexpr int NT = Tile<LS, VAR>::NT;
     constexpr int ST = ShStride<R>::V;
 
     if (a.done && *a.done) return;
@@ -534,11 +549,11 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
     if (a.rd.fin != FIN_NONE) block_reduce_finalize<NT>(nn, a.rd);
 }
 
-template <typename S, int LS, int K>
+template <typename S, int LS, int K, int VAR = 0>
 constexpr size_t hop_smem_bytes() {
     typedef typename Traits<S>::R R;
-    return ((1 + (KindTraits<K>::HASY ? 1 : 0)) * (size_t)Tile<LS>::NT * ShStride<R>::V +
-            (KindTraits<K>::HOP ? (size_t)Tile<LS>::NS * 8 * (LinkStride<R>::V + 1) : 0)) * sizeof(R);
+    return ((1 + (KindTraits<K>::HASY ? 1 : 0)) * (size_t)Tile<LS, VAR>::NT * ShStride<R>::V +
+            (KindTraits<K>::HOP ? (size_t)Tile<LS, VAR>::NS * 8 * (LinkStride<R>::V + 1) : 0)) * sizeof(R);
 }
 
 }  // namespace eofa

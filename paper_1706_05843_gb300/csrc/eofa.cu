@@ -13,7 +13,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <array>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -60,6 +62,9 @@ struct eofa_ctx {
     std::vector<double> ev_bytes;
     long launches = 0;  // kernels launched since the last reset
     int gcr_steps = 0, gcr_fallbacks = 0;  // learned-preconditioner statistics of the current solve
+    // autotuned CTA tile variant of the four inner-solver hop kinds, per precision
+    bool tuned[4] = {};
+    int tile[4][4] = {};
     // device-driven CG loops, one per inner precision
     cudaStream_t cap = nullptr;
     cudaGraphExec_t cg_exec[4] = {};
@@ -263,6 +268,7 @@ eofa_status hop(eofa_ctx* c, int prec, int kind, int out_par, VecRef in, VecRef 
     a.lk_out = c->links[prec][out_par];
     a.lk_in = c->links[prec][1 - out_par];
     a.rd = rd;
+    a.tile_var = (kind <= KIND_OE_SCHUR_DAG && c->tuned[prec]) ? c->tile[prec][kind] : 0;
     a.done = done;
     const void* coef = prec == EOFA_F64 ? (const void*)&c->c64 : (const void*)&c->c32;
     const bool tm = timed && c->timing;
@@ -323,6 +329,83 @@ eofa_status ensure_inner(eofa_ctx* c, int P) {
         (s = vec_alloc(c, P == EOFA_F64 ? EOFA_F64 : EOFA_F32, &in.x)))
         return s;
     in.ready = true;
+    return EOFA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: for each of the four inner-solver hop kinds of a precision,
+// time both CTA tile variants on this context's buffers and keep the faster.
+// Choices are cached per (precision, Ls, lattice) for every context of the
+// process; tuning happens before any CG graph is captured.
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::array<long, 5>, int> g_tune_cache;  // (prec, Ls, X*Y, Z*T, kind) -> variant
+
+eofa_status autotune(eofa_ctx* c, int P, cudaStream_t st) {
+    if (c->tuned[P]) return EOFA_OK;
+    const Geom& g = c->g;
+    bool all = true;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (int k = 0; k < 4; ++k) {
+            auto it = g_tune_cache.find({P, g.Ls, (long)g.X * g.Y, (long)g.Z * g.T, k});
+            if (it == g_tune_cache.end()) all = false;
+            else c->tile[P][k] = it->second;
+        }
+    }
+    if (all) {
+        c->tuned[P] = true;
+        return EOFA_OK;
+    }
+    // operands: the inner vectors of P, or the context's FP64 work vectors
+    VecRef odd_a, even_t, odd_b;
+    if (P == EOFA_F64) {
+        odd_a = c->x[1]; even_t = c->t[0]; odd_b = c->qo;
+    } else {
+        odd_a = c->inner[P].p; even_t = c->inner[P].t; odd_b = c->inner[P].q;
+    }
+    const size_t bytes = (size_t)c->n5 * 24 * kWidth[P];
+    for (VecRef v : {odd_a, even_t, odd_b}) {
+        CK(cudaMemsetAsync(v.d, 0, bytes, st), "memset");
+        if (v.n) CK(cudaMemsetAsync(v.n, 0, sizeof(float) * c->n5, st), "memset");
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    const VecRef none{};
+    eofa_status s = EOFA_OK;
+    for (int k = 0; k < 4 && s == EOFA_OK; ++k) {
+        const bool even_out = (k == KIND_EO_MINV || k == KIND_EO_MINV_DAG);
+        float best = 1e30f;
+        int best_v = 0;
+        for (int v = 0; v < 2 && s == EOFA_OK; ++v) {
+            c->tuned[P] = true;
+            c->tile[P][k] = v;
+            auto launch = [&]() {
+                return even_out ? hop(c, P, k, 0, odd_a, none, even_t, red(c, FIN_NONE), nullptr, st)
+                                : hop(c, P, k, 1, even_t, odd_a, odd_b, red(c, FIN_NONE), nullptr, st);
+            };
+            if ((s = launch())) break;  // warm-up
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 3 && s == EOFA_OK; ++r) s = launch();
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; best_v = v; }
+        }
+        c->tile[P][k] = best_v;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->launches = 0;
+    if (s != EOFA_OK) {
+        c->tuned[P] = false;
+        return s;
+    }
+    c->tuned[P] = true;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (int k = 0; k < 4; ++k) g_tune_cache[{P, g.Ls, (long)g.X * g.Y, (long)g.Z * g.T, k}] = c->tile[P][k];
     return EOFA_OK;
 }
 
@@ -506,6 +589,7 @@ eofa_status solve_begin(eofa_ctx* c, const double* rhs, const double* sol, const
     ss.xp = ss.P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
     eofa_status s;
     if ((s = ensure_inner(c, ss.P))) return s;
+    if ((s = autotune(c, ss.P, st)) || (s = autotune(c, EOFA_F64, st))) return s;
     c->timing = o.kernel_timing != 0;
     c->launches = 0;
     c->gcr_steps = c->gcr_fallbacks = 0;
@@ -1013,6 +1097,11 @@ const char* eofa_status_string(eofa_status s) {
 }
 
 const char* eofa_last_error(const eofa_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int eofa_tile_sites(const eofa_ctx* ctx, int prec, int kind) {
+    if (!ctx || prec < 0 || prec > 3 || kind < 0 || kind > 3) return 0;
+    return tile_sites(ctx->g.Ls, ctx->tuned[prec] ? ctx->tile[prec][kind] : 0);
+}
 
 double eofa_hop_bytes(const eofa_ctx* ctx, int prec, int with_local) {
     if (!ctx || prec < 0 || prec > 3) return 0.0;
