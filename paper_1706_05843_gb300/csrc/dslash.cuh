@@ -18,6 +18,9 @@
 //            first-order recurrence, the rank-one EOFA shift u (x) v
 //            (Eqs. Mooee_shift_p/m) and its Sherman-Morrison inverse
 //            (Eq. sherman_morrison_mobius_inv), D~ = b5 + c5 L and D~^T.
+//            The site-local kinds (M y + h: L reaches one neighbouring
+//            slice, the shift one fixed slice) skip this phase: thread
+//            (i, s) reads those slices of y itself and keeps h in registers.
 //  3. store: thread (i, s) writes its spinor back (coalesced 16-byte
 //            chunks) and contributes |out|^2 to a deterministic reduction.
 //
@@ -49,6 +52,10 @@ template <int K> struct KindTraits {
     static constexpr bool DAG = K == KIND_EO_MINV_DAG || K == KIND_OE_SCHUR_DAG || K == KIND_FULL_DAG;
     static constexpr bool PRE = K == KIND_EO_MINV || K == KIND_RECON || K == KIND_FULL;
     static constexpr bool HASY = !(K == KIND_EO_MINV || K == KIND_EO_MINV_DAG);
+    // site-local kinds: the fifth-dimension part reaches only slices s-1, s+1
+    // and the fixed slice of the rank-one shift, so each thread finishes its
+    // own 5D site without the shared-memory column phase
+    static constexpr bool PTW = K == KIND_OE_SCHUR || K == KIND_SRC || K == KIND_FULL;
 };
 
 struct HopArgs {
@@ -306,11 +313,224 @@ __device__ __forceinline__ void op_MinvT(C2<R>* v, const SCoef<R>& c, bool sh) {
 }
 
 // ---------------------------------------------------------------------------
-// the kernel
+// shared-memory staging of the 5D tile
 // ---------------------------------------------------------------------------
+// A tile row holds the 24 reals of one 5D site.  The P- half (spins 2, 3) of
+// slice s is stored in row Ls-1-s, so a column of either chirality reads its
+// mirrored coordinate (the one in which both L's are L+) in row order.
 template <typename R> struct ShStride;
 template <> struct ShStride<float> { static constexpr int V = 28; };   // 112 B rows: conflict-free float4
 template <> struct ShStride<double> { static constexpr int V = 26; };  // 208 B rows: conflict-free double2
+
+// rows of one 4D site, padded so that the 12 columns of consecutive sites
+// land on consecutive (re, im) bank pairs of a 128-byte line
+template <typename R, int LS> struct SiteStride {
+    static constexpr int MOD = 128 / (int)sizeof(R);
+    static constexpr int WANT = 24 % MOD;
+    static constexpr int V = LS * ShStride<R>::V + ((WANT - (LS * ShStride<R>::V) % MOD) + MOD) % MOD;
+};
+
+template <typename R> struct Pair;
+template <> struct Pair<float> { typedef float2 T; };
+template <> struct Pair<double> { typedef double2 T; };
+template <typename R> struct Quad;
+template <> struct Quad<float> { typedef float4 T; static constexpr int N = 4; };
+template <> struct Quad<double> { typedef double2 T; static constexpr int N = 2; };
+
+template <typename R>
+__device__ __forceinline__ C2<R> ld_pair(const R* p) {
+    const typename Pair<R>::T q = *reinterpret_cast<const typename Pair<R>::T*>(p);
+    return {q.x, q.y};
+}
+template <typename R>
+__device__ __forceinline__ void st_pair(R* p, const C2<R>& v) {
+    typename Pair<R>::T q;
+    q.x = v.re;
+    q.y = v.im;
+    *reinterpret_cast<typename Pair<R>::T*>(p) = q;
+}
+// 12 reals (one chirality half of a row) as 16-byte vectors
+template <typename R>
+__device__ __forceinline__ void st_half(R* p, const R* v) {
+    typedef typename Quad<R>::T Q;
+    constexpr int N = Quad<R>::N;
+#pragma unroll
+    for (int i = 0; i < 12 / N; ++i) {
+        Q q;
+        if constexpr (N == 4) q = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        else q = make_double2(v[2 * i], v[2 * i + 1]);
+        reinterpret_cast<Q*>(p)[i] = q;
+    }
+}
+template <typename R>
+__device__ __forceinline__ void ld_half(const R* p, R* v) {
+    typedef typename Quad<R>::T Q;
+    constexpr int N = Quad<R>::N;
+#pragma unroll
+    for (int i = 0; i < 12 / N; ++i) {
+        const Q q = reinterpret_cast<const Q*>(p)[i];
+        if constexpr (N == 4) {
+            v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+        } else {
+            v[2 * i] = q.x; v[2 * i + 1] = q.y;
+        }
+    }
+}
+
+// The fifth-dimension program of one (site, spin, colour) column, in the
+// mirrored coordinate.  hcol: the hop result (overwritten with the output),
+// ycol: the local input; consecutive slices are ST reals apart.
+template <typename R, int LS, int KIND, int ST>
+__device__ __forceinline__ void column_program(R* hcol, const R* ycol, const SCoef<R>& cf, bool shv,
+                                               R hb) {
+    typedef KindTraits<KIND> KT;
+    C2<R> v[LS];
+    if constexpr (KIND == KIND_EO_MINV) {
+#pragma unroll
+        for (int k = 0; k < LS; ++k) v[k] = ld_pair(hcol + k * ST);
+        op_Minv<R, LS>(v, cf, shv);
+        op_fwd<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
+        const R f = (R)(-0.5) * hb;
+#pragma unroll
+        for (int k = 0; k < LS; ++k) { v[k].re *= f; v[k].im *= f; }
+    } else if constexpr (KIND == KIND_EO_MINV_DAG) {
+#pragma unroll
+        for (int k = 0; k < LS; ++k) v[k] = ld_pair(hcol + k * ST);
+        op_fwdT<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
+        op_MinvT<R, LS>(v, cf, shv);
+#pragma unroll
+        for (int k = 0; k < LS; ++k) { v[k].re *= (R)-0.5; v[k].im *= (R)-0.5; }
+    } else {
+#pragma unroll
+        for (int k = 0; k < LS; ++k) v[k] = ld_pair(ycol + k * ST);
+        if constexpr (KIND == KIND_OE_SCHUR || KIND == KIND_FULL) op_M<R, LS>(v, cf, shv);
+        if constexpr (KIND == KIND_OE_SCHUR_DAG || KIND == KIND_FULL_DAG) op_MT<R, LS>(v, cf, shv);
+        if constexpr (KT::HOP) {
+            C2<R> w[LS];
+#pragma unroll
+            for (int k = 0; k < LS; ++k) w[k] = ld_pair(hcol + k * ST);
+            if constexpr (KIND == KIND_OE_SCHUR_DAG || KIND == KIND_FULL_DAG)
+                op_fwdT<R, LS>(w, cf.b5, cf.c5, cf.m * cf.c5);
+            const R f = ((KIND == KIND_FULL || KIND == KIND_FULL_DAG) ? (R)-0.5 : (R)0.5) * hb;
+#pragma unroll
+            for (int k = 0; k < LS; ++k) {
+                v[k].re += f * w[k].re;
+                v[k].im += f * w[k].im;
+            }
+        }
+        if constexpr (KIND == KIND_RECON) op_Minv<R, LS>(v, cf, shv);
+        if constexpr (KIND == KIND_LOC_DTMINV) {
+            op_Minv<R, LS>(v, cf, shv);
+            op_fwd<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
+        }
+        if constexpr (KIND == KIND_LOC_DT) op_fwd<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
+        if constexpr (KIND == KIND_LOC_DTINV) op_inv<R, LS>(v, cf.ib, cf.zb, cf.mzb, cf.wb);
+    }
+#pragma unroll
+    for (int k = 0; k < LS; ++k) st_pair(hcol + k * ST, v[k]);
+}
+
+// v <- M v for the 5D site (xcb, s) of field y, v = y(xcb, s) on entry: the
+// P+ half takes slice s-1, the P- half slice s+1 (antiperiodic through -m),
+// and the shift chirality the rank-one term sbk u_k y(last) of Eq. (Mooee_shift)
+// with k the mirrored index and "last" slice Ls-1 (P+) or 0 (P-).
+template <typename S, typename R, int LS>
+__device__ __forceinline__ void site_M(const void* __restrict__ y, const float* __restrict__ ynrm, long xcb,
+                                       int s, const SCoef<R>& cf, R* v) {
+    R q[12];
+    {
+        const int sm = (s == 0) ? LS - 1 : s - 1;
+        const R gu = (s == 0) ? -cf.m * cf.gamma : cf.gamma;
+        load_half<S, R>(y, ynrm, xcb, sm, LS, 0, q);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) v[i] = cf.alpha * v[i] + gu * q[i];
+    }
+    {
+        const int sp = (s == LS - 1) ? 0 : s + 1;
+        const R gd = (s == LS - 1) ? -cf.m * cf.gamma : cf.gamma;
+        load_half<S, R>(y, ynrm, xcb, sp, LS, 1, q);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) v[12 + i] = cf.alpha * v[12 + i] + gd * q[i];
+    }
+    if (cf.has_shift) {
+        const int cs = cf.cs;
+        load_half<S, R>(y, ynrm, xcb, cs == 0 ? LS - 1 : 0, LS, cs, q);
+        const R f = cf.sbk * cf.um[cs == 0 ? s : LS - 1 - s];
+        if (cs == 0) {
+#pragma unroll
+            for (int i = 0; i < 12; ++i) v[i] += f * q[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < 12; ++i) v[12 + i] += f * q[i];
+        }
+    }
+}
+
+// The adjoint site-local kinds (M^T y + f D~^T h) need slice s+1 (P+) and
+// s-1 (P-) of both y and h, and on the shift chirality the column sum
+// d = sum_k u_k y_k.  When Ls is a power of two the Ls threads of a 4D site
+// are one aligned lane group of a warp, and these come from warp shuffles;
+// otherwise (Ls = 12) the kind goes through the column phase.
+template <int K, int LS> struct ShflTail {
+    static constexpr bool ON = (K == KIND_OE_SCHUR_DAG || K == KIND_FULL_DAG) && LS <= 32 && (LS & (LS - 1)) == 0;
+    static constexpr bool COLS = !KindTraits<K>::PTW && !ON;
+};
+
+// o = M^T v + f (b5 + c5 L^T) h for lane s of a group of LS lanes: L^T takes
+// P+ from slice s+1 and P- from slice s-1, each with -m across the wall;
+// the rank-one part of M^T adds sbk (sum_k u_k v_k) to the last mirrored
+// slice of the shift chirality.  Every lane of the warp must call this.
+template <typename R, int LS>
+__device__ __forceinline__ void site_MT_dtT(int s, const SCoef<R>& cf, const R* v, const R* h, R f, R* o) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int up = (s + 1) & (LS - 1), dn = (s - 1) & (LS - 1);
+    const R wu = (s == LS - 1) ? -cf.m : (R)1;
+    const R wd = (s == 0) ? -cf.m : (R)1;
+    const R fb = f * cf.b5, fc = f * cf.c5;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+        const R yn = wu * __shfl_sync(FULL, v[i], up, LS);
+        const R hn = wu * __shfl_sync(FULL, h[i], up, LS);
+        o[i] = cf.alpha * v[i] + cf.gamma * yn + fb * h[i] + fc * hn;
+    }
+#pragma unroll
+    for (int i = 12; i < 24; ++i) {
+        const R yn = wd * __shfl_sync(FULL, v[i], dn, LS);
+        const R hn = wd * __shfl_sync(FULL, h[i], dn, LS);
+        o[i] = cf.alpha * v[i] + cf.gamma * yn + fb * h[i] + fc * hn;
+    }
+    if (cf.has_shift) {
+        const int cs = cf.cs;
+        const R u = cf.um[cs == 0 ? s : LS - 1 - s];
+        const bool last = s == (cs == 0 ? LS - 1 : 0);
+        R d[12];
+        if (cs == 0) {
+#pragma unroll
+            for (int i = 0; i < 12; ++i) d[i] = u * v[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < 12; ++i) d[i] = u * v[12 + i];
+        }
+#pragma unroll
+        for (int off = LS / 2; off > 0; off >>= 1) {
+#pragma unroll
+            for (int i = 0; i < 12; ++i) d[i] += __shfl_xor_sync(FULL, d[i], off, LS);
+        }
+        if (last) {
+            if (cs == 0) {
+#pragma unroll
+                for (int i = 0; i < 12; ++i) o[i] += cf.sbk * d[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 12; ++i) o[12 + i] += cf.sbk * d[i];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
 
 // one staged link: 18 reals padded to a multiple of 16 bytes
 template <typename R> struct LinkStride;
@@ -345,26 +565,30 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
     constexpr int NS = Tile<LS, VAR>::NS;
     constexpr int NT = Tile<LS, VAR>::NT;
     constexpr int ST = ShStride<R>::V;
+    constexpr int SS = SiteStride<R, LS>::V;
 
     if (a.done && *a.done) return;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* sh = reinterpret_cast<R*>(smem_raw);          // [NS*LS][ST] hop result
-    R* sy = sh + NS * LS * ST;                        // [NS*LS][ST] local input
+    constexpr bool SHF = ShflTail<KIND, LS>::ON;
+    constexpr bool COLS = ShflTail<KIND, LS>::COLS;  // column phase and its tile buffers
+    R* sh = reinterpret_cast<R*>(smem_raw);          // [NS][SS] hop result
+    R* sy = sh + (COLS ? NS * SS : 0);                // [NS][SS] local input
 
     const int tid = threadIdx.x;
     const int il = tid / LS;
     const int s = tid - il * LS;
     const long xcb = (long)blockIdx.x * NS + il;
     const bool valid = xcb < a.g.Vh;
-    const int row = il * LS + s;
+    const int rp = il * SS + s * ST;                  // row of the P+ half
+    const int rm = il * SS + (LS - 1 - s) * ST + 12;  // row of the P- half
 
     // ---------------- phase 0: links and neighbours, once per 4D site ---
     // The 8 links of each site (4 forward from this parity, 4 backward from
     // the neighbours) are loaded once, their third row rebuilt, and kept in
     // shared memory for all Ls slices of the site, together with the 8
     // neighbour indices (bit 31: the hop crosses the time boundary).
-    R* sl = sy + (KT::HASY ? NS * LS * ST : 0);   // [NS][8][LK]
+    R* sl = sy + ((KT::HASY && COLS) ? NS * SS : 0);  // [NS][8][LK]
     constexpr int LK = LinkStride<R>::V;
     unsigned* snb = reinterpret_cast<unsigned*>(sl + NS * 8 * LK);  // [NS][8]
     if constexpr (KT::HOP) {
@@ -402,11 +626,12 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
     }
 
     // ---------------- phase 1: hop and staging --------------------------
+    R o[24];    // the output spinor of this thread's 5D site
+    R acc[24];  // its hop result (zero for padding sites)
+#pragma unroll
+    for (int i = 0; i < 24; ++i) acc[i] = (R)0;
     if (valid) {
         if constexpr (KT::HOP) {
-            R acc[24];
-#pragma unroll
-            for (int i = 0; i < 24; ++i) acc[i] = (R)0;
             constexpr int FS = KT::DAG ? +1 : -1;  // forward projector 1 + FS gamma
 #pragma unroll
             for (int mu = 0; mu < 4; ++mu) {
@@ -450,100 +675,63 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
                     }
                 }
             }
+            if constexpr (KT::PTW) {
+                // out = [M] y + f h, finished in registers
+                const R f = ((KIND == KIND_FULL) ? (R)-0.5 : (R)0.5) * (KT::PRE ? cf.b5 : (R)1);
+                R v[24];
+                load_sp<S, R>(a.y, a.y_nrm, xcb, s, LS, v);
+                if constexpr (KIND != KIND_SRC) site_M<S, R, LS>(a.y, a.y_nrm, xcb, s, cf, v);
 #pragma unroll
-            for (int i = 0; i < 24; ++i) sh[row * ST + i] = acc[i];
+                for (int i = 0; i < 24; ++i) o[i] = v[i] + f * acc[i];
+            } else if constexpr (COLS) {
+                st_half(sh + rp, acc);
+                st_half(sh + rm, acc + 12);
+            }
         }
-        if constexpr (KT::HASY) {
+        if constexpr (KT::HASY && COLS) {
             R v[24];
             load_sp<S, R>(a.y, a.y_nrm, xcb, s, LS, v);
-#pragma unroll
-            for (int i = 0; i < 24; ++i) sy[row * ST + i] = v[i];
+            st_half(sy + rp, v);
+            st_half(sy + rm, v + 12);
         }
     }
-    __syncthreads();
-
-    // ---------------- phase 2: fifth-dimension program ------------------
-    // scale of the hop term (the b5 of the on-the-fly D~ folded in)
-    const R hb = KT::PRE ? cf.b5 : (R)1;
-    for (int col = tid; col < NS * 12; col += NT) {
-        const int ci = col / 12;
-        const int cc = col - ci * 12;        // spin * 3 + colour
-        const int chi = cc >= 6 ? 1 : 0;     // 0: P+, 1: P-
-        const bool shv = cf.has_shift && (chi == cf.cs);
-        const int base = ci * LS;
-        C2<R> v[LS];
-        if constexpr (KIND == KIND_EO_MINV) {
-#pragma unroll
-            for (int k = 0; k < LS; ++k) {
-                const int r = base + (chi ? LS - 1 - k : k);
-                v[k] = {sh[r * ST + 2 * cc], sh[r * ST + 2 * cc + 1]};
-            }
-            op_Minv<R, LS>(v, cf, shv);
-            op_fwd<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
-            const R f = (R)(-0.5) * hb;
-#pragma unroll
-            for (int k = 0; k < LS; ++k) { v[k].re *= f; v[k].im *= f; }
-        } else if constexpr (KIND == KIND_EO_MINV_DAG) {
-#pragma unroll
-            for (int k = 0; k < LS; ++k) {
-                const int r = base + (chi ? LS - 1 - k : k);
-                v[k] = {sh[r * ST + 2 * cc], sh[r * ST + 2 * cc + 1]};
-            }
-            op_fwdT<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
-            op_MinvT<R, LS>(v, cf, shv);
-#pragma unroll
-            for (int k = 0; k < LS; ++k) { v[k].re *= (R)-0.5; v[k].im *= (R)-0.5; }
+    if constexpr (SHF) {
+        // out = M^T y + f D~^T h with the slice neighbours from the site's lanes
+        R v[24];
+        if (valid) {
+            load_sp<S, R>(a.y, a.y_nrm, xcb, s, LS, v);
         } else {
 #pragma unroll
-            for (int k = 0; k < LS; ++k) {
-                const int r = base + (chi ? LS - 1 - k : k);
-                v[k] = {sy[r * ST + 2 * cc], sy[r * ST + 2 * cc + 1]};
-            }
-            if constexpr (KIND == KIND_OE_SCHUR || KIND == KIND_FULL) op_M<R, LS>(v, cf, shv);
-            if constexpr (KIND == KIND_OE_SCHUR_DAG || KIND == KIND_FULL_DAG) op_MT<R, LS>(v, cf, shv);
-            if constexpr (KT::HOP) {
-                C2<R> w[LS];
-#pragma unroll
-                for (int k = 0; k < LS; ++k) {
-                    const int r = base + (chi ? LS - 1 - k : k);
-                    w[k] = {sh[r * ST + 2 * cc], sh[r * ST + 2 * cc + 1]};
-                }
-                if constexpr (KIND == KIND_OE_SCHUR_DAG || KIND == KIND_FULL_DAG)
-                    op_fwdT<R, LS>(w, cf.b5, cf.c5, cf.m * cf.c5);
-                const R f = ((KIND == KIND_FULL || KIND == KIND_FULL_DAG) ? (R)-0.5 : (R)0.5) * hb;
-#pragma unroll
-                for (int k = 0; k < LS; ++k) {
-                    v[k].re += f * w[k].re;
-                    v[k].im += f * w[k].im;
-                }
-            }
-            if constexpr (KIND == KIND_RECON) op_Minv<R, LS>(v, cf, shv);
-            if constexpr (KIND == KIND_LOC_DTMINV) {
-                op_Minv<R, LS>(v, cf, shv);
-                op_fwd<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
-            }
-            if constexpr (KIND == KIND_LOC_DT) op_fwd<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
-            if constexpr (KIND == KIND_LOC_DTINV) op_inv<R, LS>(v, cf.ib, cf.zb, cf.mzb, cf.wb);
+            for (int i = 0; i < 24; ++i) v[i] = (R)0;
         }
-#pragma unroll
-        for (int k = 0; k < LS; ++k) {
-            const int r = base + (chi ? LS - 1 - k : k);
-            sh[r * ST + 2 * cc] = v[k].re;
-            sh[r * ST + 2 * cc + 1] = v[k].im;
-        }
+        const R f = (KIND == KIND_FULL_DAG) ? (R)-0.5 : (R)0.5;
+        site_MT_dtT<R, LS>(s, cf, v, acc, f, o);
     }
-    __syncthreads();
+
+    // ---------------- phase 2: fifth-dimension program ------------------
+    if constexpr (COLS) {
+        __syncthreads();
+        const R hb = KT::PRE ? cf.b5 : (R)1;  // the b5 of the on-the-fly D~
+        for (int col = tid; col < NS * 12; col += NT) {
+            const int ci = col / 12;
+            const int cc = col - ci * 12;     // spin * 3 + colour
+            const bool shv = cf.has_shift && ((cc >= 6 ? 1 : 0) == cf.cs);
+            column_program<R, LS, KIND, ST>(sh + ci * SS + 2 * cc, sy + ci * SS + 2 * cc, cf, shv, hb);
+        }
+        __syncthreads();
+    }
 
     // ---------------- phase 3: store + reduction ------------------------
     R nn = (R)0;
     if (valid) {
-        R v[24];
-#pragma unroll
-        for (int i = 0; i < 24; ++i) v[i] = sh[row * ST + i];
-        store_sp<S, R>(a.out, a.out_nrm, xcb, s, LS, v);
+        if constexpr (COLS) {
+            ld_half(sh + rp, o);
+            ld_half(sh + rm, o + 12);
+        }
+        store_sp<S, R>(a.out, a.out_nrm, xcb, s, LS, o);
         if (a.rd.fin != FIN_NONE) {
 #pragma unroll
-            for (int i = 0; i < 24; ++i) nn += v[i] * v[i];
+            for (int i = 0; i < 24; ++i) nn += o[i] * o[i];
         }
     }
     if (a.rd.fin != FIN_NONE) block_reduce_finalize<NT>(nn, a.rd);
@@ -552,7 +740,8 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
 template <typename S, int LS, int K, int VAR = 0>
 constexpr size_t hop_smem_bytes() {
     typedef typename Traits<S>::R R;
-    return ((1 + (KindTraits<K>::HASY ? 1 : 0)) * (size_t)Tile<LS, VAR>::NT * ShStride<R>::V +
+    constexpr size_t bufs = ShflTail<K, LS>::COLS ? (1 + (KindTraits<K>::HASY ? 1 : 0)) : 0;
+    return (bufs * (size_t)Tile<LS, VAR>::NS * SiteStride<R, LS>::V +
             (KindTraits<K>::HOP ? (size_t)Tile<LS, VAR>::NS * 8 * (LinkStride<R>::V + 1) : 0)) * sizeof(R);
 }
 
