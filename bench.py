@@ -366,6 +366,7 @@ def run_ours(args):
     hop_bytes = sum(s["hop_bytes"] for s in stats)
     hop_n = sum(s["hop_launches"] for s in stats)
     launches = int(statistics.median([s["kernel_launches"] for s in stats]))
+    tiles = [B.lib().eofa_tile_variant(solver.ctx, B.PREC[args.inner], k) for k in range(4)]
 
     # end to end through the public API: pinned host rhs -> device, solve, -> host
     host_rhs = torch.from_numpy(phi).pin_memory()
@@ -420,6 +421,7 @@ def run_ours(args):
                 "kernel": f"hop_kernel<{args.inner}, Ls=16> (4 kinds: Schur and Schur^dag halves)",
                 "bytes_per_launch": hop_bytes / hop_n if hop_n else None,
                 "launch_ms": hop_ms / hop_n if hop_n else None, "launches_timed": hop_n,
+                "tile_variants": tiles,
                 "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
     cpu = None
     if ws == 1 and not args.no_cpu:

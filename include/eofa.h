@@ -277,6 +277,12 @@ double eofa_hop_bytes(const eofa_ctx *ctx, int prec, int with_local);
  * buffers at its first solve in a precision and cached per lattice shape. */
 int eofa_tile_sites(const eofa_ctx *ctx, int prec, int kind);
 
+/* The tile variant chosen for the same kernel: bit 0 set for the
+ * alternative CTA shape, bit 1 set when the kernel is compiled for 64
+ * registers per thread (more resident warps; FP32 arithmetic only).
+ * 0 before the first solve in that precision, -1 for invalid arguments. */
+int eofa_tile_variant(const eofa_ctx *ctx, int prec, int kind);
+
 #ifdef __cplusplus
 }
 #endif

@@ -93,6 +93,7 @@ SIGNATURES = {
     "eofa_last_error": ([_vp], C.c_char_p),
     "eofa_hop_bytes": ([_vp, C.c_int, C.c_int], C.c_double),
     "eofa_tile_sites": ([_vp, C.c_int, C.c_int], C.c_int),
+    "eofa_tile_variant": ([_vp, C.c_int, C.c_int], C.c_int),
 }
 
 _lib = None

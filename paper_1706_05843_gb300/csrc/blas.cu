@@ -25,6 +25,7 @@ __global__ void k_scal_init(DevScal* sc, double target_rr, int max_iters, unsign
     sc->target_rr = target_rr;
     sc->iters = 0;
     sc->done = 0;
+    sc->stop = 0;
     sc->nonfinite = 0;
     sc->max_iters = max_iters;
     sc->timeout_ns = timeout_ns;
@@ -96,11 +97,13 @@ __global__ void k_inner_init(DevScal* sc, double tol, double floor_tol) {
     const double rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
     if (sc->skip || !(rel > tol)) {
         sc->done = 1;
+        sc->stop = 1;
         return;
     }
     const double t = fmax(tol / rel, floor_tol);
     sc->target_rr = t * t;
     sc->done = 0;
+    sc->stop = 0;
 }
 
 cudaError_t inner_init(DevScal* sc, double tol, double floor_tol, cudaStream_t st) {
@@ -111,51 +114,62 @@ cudaError_t inner_init(DevScal* sc, double tol, double floor_tol, cudaStream_t s
 // ---------------------------------------------------------------------------
 // CG updates
 // ---------------------------------------------------------------------------
-template <typename S, typename SX>
-__global__ void __launch_bounds__(BT) k_cg_xr(VecRef x, VecRef p, VecRef q, VecRef r, long n5, int Ls,
-                                              Reduce rd, const int* done) {
+// r -= alpha q and |r|^2 (FIN_RR: convergence test and iteration count)
+template <typename S>
+__global__ void __launch_bounds__(BT) k_cg_r(VecRef q, VecRef r, long n5, int Ls, Reduce rd, const int* done) {
     typedef typename Traits<S>::R R;
-    typedef typename Traits<SX>::R RX;
     if (*done) return;
     const long t = (long)blockIdx.x * BT + threadIdx.x;
     R nn = (R)0;
     if (t < n5) {
         const long xcb = t / Ls;
         const int s = (int)(t - xcb * Ls);
-        const double al = rd.scal->alpha;
-        R pv[24], qv[24], rv[24];
-        RX xv[24];
-        load_sp<S, R>(p.d, p.n, xcb, s, Ls, pv);
+        const R al = (R)rd.scal->alpha;
+        R qv[24], rv[24];
         load_sp<S, R>(q.d, q.n, xcb, s, Ls, qv);
         load_sp<S, R>(r.d, r.n, xcb, s, Ls, rv);
-        load_sp<SX, RX>(x.d, x.n, xcb, s, Ls, xv);
 #pragma unroll
         for (int i = 0; i < 24; ++i) {
-            xv[i] += (RX)al * (RX)pv[i];
-            rv[i] -= (R)al * qv[i];
+            rv[i] -= al * qv[i];
             nn += rv[i] * rv[i];
         }
-        store_sp<SX, RX>(x.d, x.n, xcb, s, Ls, xv);
         store_sp<S, R>(r.d, r.n, xcb, s, Ls, rv);
     }
     block_reduce_finalize<BT>(nn, rd);
 }
 
-template <typename S>
-__global__ void __launch_bounds__(BT) k_cg_p(VecRef p, VecRef z, long n5, int Ls, const DevScal* sc) {
+// x += alpha p, then p = z + beta p, sharing the read of p.  The update of
+// x belongs to the iteration whose residual update ran, so it still runs in
+// the iteration that set the done flag; the last block then sets stop
+// (FIN_STOP), which ends this kernel in the iterations that follow.
+template <typename S, typename SX>
+__global__ void __launch_bounds__(BT) k_cg_px(VecRef x, VecRef p, VecRef z, long n5, int Ls, Reduce rd) {
     typedef typename Traits<S>::R R;
-    if (sc->done) return;
+    typedef typename Traits<SX>::R RX;
+    const DevScal* sc = rd.scal;
+    if (sc->stop) return;
     const long t = (long)blockIdx.x * BT + threadIdx.x;
-    if (t >= n5) return;
-    const long xcb = t / Ls;
-    const int s = (int)(t - xcb * Ls);
-    const R be = (R)sc->beta;
-    R pv[24], zv[24];
-    load_sp<S, R>(p.d, p.n, xcb, s, Ls, pv);
-    load_sp<S, R>(z.d, z.n, xcb, s, Ls, zv);
+    if (t < n5) {
+        const long xcb = t / Ls;
+        const int s = (int)(t - xcb * Ls);
+        const double al = sc->alpha;
+        R pv[24];
+        RX xv[24];
+        load_sp<S, R>(p.d, p.n, xcb, s, Ls, pv);
+        load_sp<SX, RX>(x.d, x.n, xcb, s, Ls, xv);
 #pragma unroll
-    for (int i = 0; i < 24; ++i) pv[i] = zv[i] + be * pv[i];
-    store_sp<S, R>(p.d, p.n, xcb, s, Ls, pv);
+        for (int i = 0; i < 24; ++i) xv[i] += (RX)al * (RX)pv[i];
+        store_sp<SX, RX>(x.d, x.n, xcb, s, Ls, xv);
+        if (!sc->done) {
+            const R be = (R)sc->beta;
+            R zv[24];
+            load_sp<S, R>(z.d, z.n, xcb, s, Ls, zv);
+#pragma unroll
+            for (int i = 0; i < 24; ++i) pv[i] = zv[i] + be * pv[i];
+            store_sp<S, R>(p.d, p.n, xcb, s, Ls, pv);
+        }
+    }
+    block_reduce_finalize<BT>((R)0, rd);
 }
 
 // dst = a * src (types may differ); optional |dst|^2 reduction.
@@ -368,20 +382,21 @@ static cudaError_t dispatch_prec(int prec, F&& f) {
     }
 }
 
-cudaError_t blas_cg_xr(int prec, int xprec, VecRef x, VecRef p, VecRef q, VecRef r, long n5, int Ls,
-                       Reduce rd, const int* done, cudaStream_t st) {
+cudaError_t blas_cg_r(int prec, VecRef q, VecRef r, long n5, int Ls, Reduce rd, const int* done,
+                      cudaStream_t st) {
     return dispatch_prec(prec, [&](auto* tag) -> cudaError_t {
         typedef std::remove_pointer_t<decltype(tag)> S;
-        if (xprec == 0) k_cg_xr<S, double><<<grid_for(n5), BT, 0, st>>>(x, p, q, r, n5, Ls, rd, done);
-        else k_cg_xr<S, float><<<grid_for(n5), BT, 0, st>>>(x, p, q, r, n5, Ls, rd, done);
+        k_cg_r<S><<<grid_for(n5), BT, 0, st>>>(q, r, n5, Ls, rd, done);
         return cudaGetLastError();
     });
 }
 
-cudaError_t blas_cg_p(int prec, VecRef p, VecRef z, long n5, int Ls, const DevScal* sc, cudaStream_t st) {
+cudaError_t blas_cg_px(int prec, int xprec, VecRef x, VecRef p, VecRef z, long n5, int Ls, Reduce rd,
+                       cudaStream_t st) {
     return dispatch_prec(prec, [&](auto* tag) -> cudaError_t {
         typedef std::remove_pointer_t<decltype(tag)> S;
-        k_cg_p<S><<<grid_for(n5), BT, 0, st>>>(p, z, n5, Ls, sc);
+        if (xprec == 0) k_cg_px<S, double><<<grid_for(n5), BT, 0, st>>>(x, p, z, n5, Ls, rd);
+        else k_cg_px<S, float><<<grid_for(n5), BT, 0, st>>>(x, p, z, n5, Ls, rd);
         return cudaGetLastError();
     });
 }

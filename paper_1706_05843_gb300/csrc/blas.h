@@ -20,6 +20,9 @@ cudaError_t launch_hop_f64(int kind, const HopArgs& a, const void* coef, cudaStr
 cudaError_t launch_hop_f32(int kind, const HopArgs& a, const void* coef, cudaStream_t st);
 cudaError_t launch_hop_f16(int kind, const HopArgs& a, const void* coef, cudaStream_t st);
 cudaError_t launch_hop_bf16(int kind, const HopArgs& a, const void* coef, cudaStream_t st);
+// kinds >= 4 (FP64 and FP32 storage only)
+cudaError_t launch_hop_f64_outer(int kind, const HopArgs& a, const void* coef, cudaStream_t st);
+cudaError_t launch_hop_f32_outer(int kind, const HopArgs& a, const void* coef, cudaStream_t st);
 
 cudaError_t scal_init(DevScal* sc, double target_rr, int max_iters, unsigned long long timeout_ns,
                       cudaStream_t st);
@@ -27,9 +30,12 @@ cudaError_t while_cond(cudaGraphConditionalHandle h, DevScal* sc, cudaStream_t s
 cudaError_t while_cond_all(cudaGraphConditionalHandle h, const ScalList& L, cudaStream_t st);
 cudaError_t inner_ctl(DevScal* sc, int skip, int max_iters, cudaStream_t st);
 cudaError_t inner_init(DevScal* sc, double tol, double floor_tol, cudaStream_t st);
-cudaError_t blas_cg_xr(int prec, int xprec, VecRef x, VecRef p, VecRef q, VecRef r, long n5, int Ls,
-                       Reduce rd, const int* done, cudaStream_t st);
-cudaError_t blas_cg_p(int prec, VecRef p, VecRef z, long n5, int Ls, const DevScal* sc, cudaStream_t st);
+// r -= alpha q with |r|^2 (rd: FIN_RR); returns at once when *done
+cudaError_t blas_cg_r(int prec, VecRef q, VecRef r, long n5, int Ls, Reduce rd, const int* done,
+                      cudaStream_t st);
+// x += alpha p; p = z + beta p unless done (rd: FIN_STOP on the same scalars)
+cudaError_t blas_cg_px(int prec, int xprec, VecRef x, VecRef p, VecRef z, long n5, int Ls, Reduce rd,
+                       cudaStream_t st);
 cudaError_t blas_copy(int dprec, VecRef dst, int sprec, VecRef src, long n5, int Ls, double scale,
                       int inv_sqrt_slot, Reduce rd, cudaStream_t st);
 cudaError_t blas_acc(VecRef x, int eprec, VecRef e, long n5, int Ls, const DevScal* sc, int slot,

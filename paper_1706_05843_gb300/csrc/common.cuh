@@ -71,6 +71,7 @@ struct DevScal {
     unsigned long long timeout_ns; // 0: none
     int timed_out;
     int skip;                      // batched solves: this system sits the round out
+    int stop;                      // the CG update of x and p has run after done was set
 };
 
 // the device scalars of up to 32 systems (one batched graph)
@@ -79,7 +80,7 @@ struct ScalList {
     int n;
 };
 
-enum Fin { FIN_NONE = 0, FIN_STORE = 1, FIN_ALPHA = 2, FIN_BETA = 3, FIN_RR = 4, FIN_ZZ = 5 };
+enum Fin { FIN_NONE = 0, FIN_STORE = 1, FIN_ALPHA = 2, FIN_BETA = 3, FIN_RR = 4, FIN_ZZ = 5, FIN_STOP = 6 };
 
 struct Reduce {
     double* partials;   // one per block
@@ -355,6 +356,7 @@ __device__ __forceinline__ void finalize(const Reduce& rd, double total) {
             sc->zz = total;
             break;
         case FIN_ZZ: sc->zz = total; break;
+        case FIN_STOP: sc->stop = sc->done; break;
         case FIN_RR:
             sc->rr = total;
             sc->iters += 1;

@@ -537,29 +537,38 @@ template <typename R> struct LinkStride;
 template <> struct LinkStride<float> { static constexpr int V = 20; };
 template <> struct LinkStride<double> { static constexpr int V = 18; };
 
-// CTA tile: NS 4D sites x Ls slices, one thread per 5D site.  Variant 0 is
-// the default; variant 1 (twice the sites, or half for Ls = 12) is the
-// alternative the autotuner times against it for the inner-solver kinds.
+// CTA tile: NS 4D sites x Ls slices, one thread per 5D site.  Bit 0 of the
+// variant picks the shape: 0 the default, 1 twice the sites (half for
+// Ls = 12).  Bit 1 asks for 64 registers per thread (more resident warps,
+// a few spilled values) and applies to FP32 arithmetic only.  The
+// autotuner times the variants for the inner-solver kinds.
 template <int LS, int VAR = 0> struct Tile {
     static constexpr int NS0 = (LS >= 16) ? 8 : (LS == 12 ? 16 : 128 / LS);
-    static constexpr int NS = VAR == 0 ? NS0 : (LS == 12 ? NS0 / 2 : NS0 * 2);
+    static constexpr int NS = (VAR & 1) == 0 ? NS0 : (LS == 12 ? NS0 / 2 : NS0 * 2);
     static constexpr int NT = NS * LS;
+};
+
+template <typename S> constexpr int kTileVariants = sizeof(typename Traits<S>::R) == 4 ? 4 : 2;
+
+// the register-capped variants ask for this many resident CTAs per SM
+template <int LS, int VAR> struct MinBlocks64 {
+    static constexpr int V = 65536 / (64 * Tile<LS, VAR>::NT);
 };
 
 // sites per CTA of a tile variant (for reports)
 inline int tile_sites(int Ls, int var) {
+    const bool alt = var & 1;
     switch (Ls) {
-        case 4: return var ? Tile<4, 1>::NS : Tile<4, 0>::NS;
-        case 8: return var ? Tile<8, 1>::NS : Tile<8, 0>::NS;
-        case 12: return var ? Tile<12, 1>::NS : Tile<12, 0>::NS;
-        case 16: return var ? Tile<16, 1>::NS : Tile<16, 0>::NS;
+        case 4: return alt ? Tile<4, 1>::NS : Tile<4, 0>::NS;
+        case 8: return alt ? Tile<8, 1>::NS : Tile<8, 0>::NS;
+        case 12: return alt ? Tile<12, 1>::NS : Tile<12, 0>::NS;
+        case 16: return alt ? Tile<16, 1>::NS : Tile<16, 0>::NS;
         default: return 0;
     }
 }
 
-template <typename S, int LS, int KIND, int VAR = 0>
-__global__ void __launch_bounds__(Tile<LS, VAR>::NT)
-hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
+template <typename S, int LS, int KIND, int VAR>
+__device__ __forceinline__ void hop_body(const HopArgs& a, const SCoef<typename Traits<S>::R>& cf) {
     typedef typename Traits<S>::R R;
     typedef KindTraits<KIND> KT;
     constexpr int NS = Tile<LS, VAR>::NS;
@@ -735,6 +744,19 @@ hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
         }
     }
     if (a.rd.fin != FIN_NONE) block_reduce_finalize<NT>(nn, a.rd);
+}
+
+// the kernel with the compiler's own register choice (variants 0, 1) ...
+template <typename S, int LS, int KIND, int VAR = 0>
+__global__ void __launch_bounds__(Tile<LS, VAR>::NT) hop_kernel(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
+    hop_body<S, LS, KIND, VAR>(a, cf);
+}
+
+// ... and with 64 registers per thread (variants 2, 3; FP32 arithmetic)
+template <typename S, int LS, int KIND, int VAR>
+__global__ void __launch_bounds__(Tile<LS, VAR>::NT, MinBlocks64<LS, VAR>::V)
+    hop_kernel_r64(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
+    hop_body<S, LS, KIND, VAR>(a, cf);
 }
 
 template <typename S, int LS, int K, int VAR = 0>

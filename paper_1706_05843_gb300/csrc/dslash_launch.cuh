@@ -1,8 +1,11 @@
 // dslash_launch.cuh -- host-side dispatch of hop_kernel over (Ls, kind, tile
-// variant) for one storage type.  Included once per storage type by
-// dslash_<prec>.cu so the four precisions compile as separate translation
-// units.  The four kinds of the inner CG (the Schur complement and its
-// adjoint) exist in two tile variants for the autotuner; the others in one.
+// variant) for one storage type.  Included by dslash_<prec>.cu (the four
+// kinds of the inner CG: the Schur complement and its adjoint) and by
+// dslash_<prec>_outer.cu (the FP64/FP32 outer-solver kinds), so the kernel
+// instantiations compile as separate translation units.  The inner kinds
+// exist in every tile variant the autotuner times (two CTA shapes, and for
+// FP32 arithmetic each with and without a 64-register cap); the others in
+// the default variant only.
 #pragma once
 
 #include "dslash.cuh"
@@ -12,62 +15,94 @@ namespace eofa {
 template <typename S, int LS, int K, int VAR>
 static cudaError_t launch_one(const HopArgs& a, const SCoef<typename Traits<S>::R>& c,
                               cudaStream_t st) {
-    constexpr int NT = Tile<LS, VAR>::NT;
     constexpr int NS = Tile<LS, VAR>::NS;
+    constexpr int NT = Tile<LS, VAR>::NT;
     const size_t smem = hop_smem_bytes<S, LS, K, VAR>();
+    constexpr bool R64 = (VAR & 2) != 0;
     static bool attr_done = false;  // per instantiation; set before first launch
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(hop_kernel<S, LS, K, VAR>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e;
+        if constexpr (R64)
+            e = cudaFuncSetAttribute(hop_kernel_r64<S, LS, K, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+        else
+            e = cudaFuncSetAttribute(hop_kernel<S, LS, K, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
     const int grid = (a.g.Vh + NS - 1) / NS;
     if (grid == 0) return cudaSuccess;
-    hop_kernel<S, LS, K, VAR><<<grid, NT, smem, st>>>(a, c);
+    if constexpr (R64) hop_kernel_r64<S, LS, K, VAR><<<grid, NT, smem, st>>>(a, c);
+    else hop_kernel<S, LS, K, VAR><<<grid, NT, smem, st>>>(a, c);
     return cudaGetLastError();
 }
 
 template <typename S, int LS, int K>
 static cudaError_t launch_var(const HopArgs& a, const SCoef<typename Traits<S>::R>& c, cudaStream_t st) {
-    return a.tile_var == 1 ? launch_one<S, LS, K, 1>(a, c, st) : launch_one<S, LS, K, 0>(a, c, st);
+    if constexpr (kTileVariants<S> == 4) {
+        switch (a.tile_var) {
+            case 1: return launch_one<S, LS, K, 1>(a, c, st);
+            case 2: return launch_one<S, LS, K, 2>(a, c, st);
+            case 3: return launch_one<S, LS, K, 3>(a, c, st);
+            default: return launch_one<S, LS, K, 0>(a, c, st);
+        }
+    } else {
+        return (a.tile_var & 1) ? launch_one<S, LS, K, 1>(a, c, st) : launch_one<S, LS, K, 0>(a, c, st);
+    }
 }
 
 template <typename S, int LS>
-static cudaError_t launch_ls(int kind, const HopArgs& a, const SCoef<typename Traits<S>::R>& c,
-                             cudaStream_t st) {
-    constexpr bool LOWP = sizeof(S) == 2;
+static cudaError_t launch_inner_ls(int kind, const HopArgs& a, const SCoef<typename Traits<S>::R>& c,
+                                   cudaStream_t st) {
     switch (kind) {
         case KIND_EO_MINV: return launch_var<S, LS, KIND_EO_MINV>(a, c, st);
         case KIND_OE_SCHUR: return launch_var<S, LS, KIND_OE_SCHUR>(a, c, st);
         case KIND_EO_MINV_DAG: return launch_var<S, LS, KIND_EO_MINV_DAG>(a, c, st);
         case KIND_OE_SCHUR_DAG: return launch_var<S, LS, KIND_OE_SCHUR_DAG>(a, c, st);
-        default: break;
+        default: return cudaErrorNotSupported;
     }
-    if constexpr (!LOWP) {
-        switch (kind) {
-            case KIND_RECON: return launch_one<S, LS, KIND_RECON, 0>(a, c, st);
-            case KIND_SRC: return launch_one<S, LS, KIND_SRC, 0>(a, c, st);
-            case KIND_FULL: return launch_one<S, LS, KIND_FULL, 0>(a, c, st);
-            case KIND_FULL_DAG: return launch_one<S, LS, KIND_FULL_DAG, 0>(a, c, st);
-            case KIND_LOC_DTMINV: return launch_one<S, LS, KIND_LOC_DTMINV, 0>(a, c, st);
-            case KIND_LOC_DT: return launch_one<S, LS, KIND_LOC_DT, 0>(a, c, st);
-            case KIND_LOC_DTINV: return launch_one<S, LS, KIND_LOC_DTINV, 0>(a, c, st);
-            default: break;
-        }
-    }
-    return cudaErrorNotSupported;
 }
 
+template <typename S, int LS>
+static cudaError_t launch_outer_ls(int kind, const HopArgs& a, const SCoef<typename Traits<S>::R>& c,
+                                   cudaStream_t st) {
+    switch (kind) {
+        case KIND_RECON: return launch_one<S, LS, KIND_RECON, 0>(a, c, st);
+        case KIND_SRC: return launch_one<S, LS, KIND_SRC, 0>(a, c, st);
+        case KIND_FULL: return launch_one<S, LS, KIND_FULL, 0>(a, c, st);
+        case KIND_FULL_DAG: return launch_one<S, LS, KIND_FULL_DAG, 0>(a, c, st);
+        case KIND_LOC_DTMINV: return launch_one<S, LS, KIND_LOC_DTMINV, 0>(a, c, st);
+        case KIND_LOC_DT: return launch_one<S, LS, KIND_LOC_DT, 0>(a, c, st);
+        case KIND_LOC_DTINV: return launch_one<S, LS, KIND_LOC_DTINV, 0>(a, c, st);
+        default: return cudaErrorNotSupported;
+    }
+}
+
+// kinds 0..3 (every storage type)
 template <typename S>
-static cudaError_t launch_hop_t(int kind, const HopArgs& a, const void* coef, cudaStream_t st) {
+static cudaError_t launch_inner_t(int kind, const HopArgs& a, const void* coef, cudaStream_t st) {
     typedef typename Traits<S>::R R;
     const SCoef<R>& c = *reinterpret_cast<const SCoef<R>*>(coef);
     switch (a.g.Ls) {
-        case 4: return launch_ls<S, 4>(kind, a, c, st);
-        case 8: return launch_ls<S, 8>(kind, a, c, st);
-        case 12: return launch_ls<S, 12>(kind, a, c, st);
-        case 16: return launch_ls<S, 16>(kind, a, c, st);
+        case 4: return launch_inner_ls<S, 4>(kind, a, c, st);
+        case 8: return launch_inner_ls<S, 8>(kind, a, c, st);
+        case 12: return launch_inner_ls<S, 12>(kind, a, c, st);
+        case 16: return launch_inner_ls<S, 16>(kind, a, c, st);
+        default: return cudaErrorNotSupported;
+    }
+}
+
+// kinds 4..10 (FP64 and FP32 storage)
+template <typename S>
+static cudaError_t launch_outer_t(int kind, const HopArgs& a, const void* coef, cudaStream_t st) {
+    typedef typename Traits<S>::R R;
+    const SCoef<R>& c = *reinterpret_cast<const SCoef<R>*>(coef);
+    switch (a.g.Ls) {
+        case 4: return launch_outer_ls<S, 4>(kind, a, c, st);
+        case 8: return launch_outer_ls<S, 8>(kind, a, c, st);
+        case 12: return launch_outer_ls<S, 12>(kind, a, c, st);
+        case 16: return launch_outer_ls<S, 16>(kind, a, c, st);
         default: return cudaErrorNotSupported;
     }
 }

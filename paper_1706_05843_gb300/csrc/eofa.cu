@@ -376,24 +376,30 @@ eofa_status autotune(eofa_ctx* c, int P, cudaStream_t st) {
     eofa_status s = EOFA_OK;
     for (int k = 0; k < 4 && s == EOFA_OK; ++k) {
         const bool even_out = (k == KIND_EO_MINV || k == KIND_EO_MINV_DAG);
-        float best = 1e30f;
-        int best_v = 0;
-        for (int v = 0; v < 2 && s == EOFA_OK; ++v) {
-            c->tuned[P] = true;
-            c->tile[P][k] = v;
-            auto launch = [&]() {
-                return even_out ? hop(c, P, k, 0, odd_a, none, even_t, red(c, FIN_NONE), nullptr, st)
-                                : hop(c, P, k, 1, even_t, odd_a, odd_b, red(c, FIN_NONE), nullptr, st);
-            };
-            if ((s = launch())) break;  // warm-up
-            cudaEventRecord(e0, st);
-            for (int r = 0; r < 3 && s == EOFA_OK; ++r) s = launch();
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; best_v = v; }
+        const int nvar = (P == EOFA_F64) ? 2 : 4;  // register-capped variants for FP32 arithmetic
+        float best[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+        // three interleaved rounds; each variant keeps its fastest round
+        for (int round = 0; round < 3 && s == EOFA_OK; ++round) {
+            for (int v = 0; v < nvar && s == EOFA_OK; ++v) {
+                c->tuned[P] = true;
+                c->tile[P][k] = v;
+                auto launch = [&]() {
+                    return even_out ? hop(c, P, k, 0, odd_a, none, even_t, red(c, FIN_NONE), nullptr, st)
+                                    : hop(c, P, k, 1, even_t, odd_a, odd_b, red(c, FIN_NONE), nullptr, st);
+                };
+                if ((s = launch())) break;  // warm-up
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 3 && s == EOFA_OK; ++r) s = launch();
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                best[v] = std::min(best[v], ms);
+            }
         }
+        int best_v = 0;
+        for (int v = 1; v < nvar; ++v)
+            if (best[v] < best[best_v]) best_v = v;
         c->tile[P][k] = best_v;
     }
     cudaEventDestroy(e0);
@@ -427,10 +433,10 @@ eofa_status cg_iteration(eofa_ctx* c, int P, cudaStream_t st, bool timed) {
     eofa_status s;
     if ((s = hop(c, P, KIND_EO_MINV, 0, in.p, none, in.t, red(c, FIN_NONE), done, st, timed))) return s;
     if ((s = hop(c, P, KIND_OE_SCHUR, 1, in.t, in.p, in.q, red(c, FIN_ALPHA), done, st, timed))) return s;
-    CKL(blas_cg_xr(P, xp, in.x, in.p, in.q, in.r, c->n5, c->g.Ls, red(c, FIN_RR), done, st), "cg_xr");
+    CKL(blas_cg_r(P, in.q, in.r, c->n5, c->g.Ls, red(c, FIN_RR), done, st), "cg_r");
     if ((s = hop(c, P, KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), done, st, timed))) return s;
     if ((s = hop(c, P, KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_BETA), done, st, timed))) return s;
-    CKL(blas_cg_p(P, in.p, in.z, c->n5, c->g.Ls, c->scal, st), "cg_p");
+    CKL(blas_cg_px(P, xp, in.x, in.p, in.z, c->n5, c->g.Ls, red(c, FIN_STOP), st), "cg_px");
     return EOFA_OK;
 }
 
@@ -562,6 +568,7 @@ struct SolveState {
     int total = 0, outer = 0;
     eofa_status result = EOFA_ERR_NOT_CONVERGED;
     bool finished = false;
+    bool x_zero = false;  // odd solution still zero: the outer residual is the source itself
 };
 
 eofa_status enqueue_read(eofa_ctx* c, cudaStream_t st) {
@@ -613,6 +620,7 @@ eofa_status solve_begin(eofa_ctx* c, const double* rhs, const double* sol, const
         }
     } else {
         CKL(blas_zero(0, c->x[1], c->n5, Ls, st), "zero");
+        ss.x_zero = true;
     }
     if ((s = hop(c, 0, KIND_LOC_DTMINV, 0, none, c->b[0], c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
     if ((s = hop(c, 0, KIND_SRC, 1, c->t[0], c->b[1], c->bto, red(c, FIN_NONE), nullptr, st))) return s;
@@ -633,7 +641,11 @@ eofa_status solve_check_rhs(eofa_ctx* c, double* sol, SolveState& ss, cudaStream
 }
 
 // r = b~o - S x_o in FP64 with |r|^2 into store[0]; read-back enqueued.
-eofa_status outer_residual(eofa_ctx* c, cudaStream_t st) {
+eofa_status outer_residual(eofa_ctx* c, const SolveState& ss, cudaStream_t st) {
+    if (ss.x_zero) {  // r = b~o - S 0
+        CKL(blas_copy(0, c->ro, 0, c->bto, c->n5, c->g.Ls, 1.0, -1, red(c, FIN_STORE, 0), st), "copy");
+        return enqueue_read(c, st);
+    }
     const VecRef none{};
     eofa_status s;
     if ((s = hop(c, 0, KIND_EO_MINV, 0, c->x[1], none, c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
@@ -725,7 +737,7 @@ eofa_status solve_impl(eofa_ctx* c, const double* rhs, double* sol, const eofa_s
     if ((s = solve_check_rhs(c, sol, ss, st))) return s;
     const int Ls = c->g.Ls;
     while (!ss.finished) {
-        if ((s = outer_residual(c, st))) return s;
+        if ((s = outer_residual(c, ss, st))) return s;
         CK(cudaStreamSynchronize(st), "sync");
         if (!outer_decide(c, o, ss)) break;
         const double itol = std::max(o.tol / ss.rel, inner_tol_floor(o, ss.P));
@@ -743,6 +755,7 @@ eofa_status solve_impl(eofa_ctx* c, const double* rhs, double* sol, const eofa_s
             break;
         }
         CKL(blas_acc(c->x[1], ss.xp, c->inner[ss.P].x, c->n5, Ls, c->scal, 0, st), "acc");
+        ss.x_zero = false;
     }
     return solve_end(c, sol, o, ss, stats, st);
 }
@@ -871,7 +884,7 @@ eofa_status solve_batched_impl(eofa_ctx* const* cs, int n, const void* const* rh
     for (;;) {
         int active = 0;
         for (int i = 0; i < n; ++i)
-            if (!ss[i].finished && (s = outer_residual(cs[i], st))) { cudaGraphExecDestroy(exec); return s; }
+            if (!ss[i].finished && (s = outer_residual(cs[i], ss[i], st))) { cudaGraphExecDestroy(exec); return s; }
         if (cudaStreamSynchronize(st) != cudaSuccess) { cudaGraphExecDestroy(exec); return EOFA_ERR_CUDA; }
         for (int i = 0; i < n; ++i) {
             if (ss[i].finished) continue;
@@ -901,6 +914,7 @@ eofa_status solve_batched_impl(eofa_ctx* const* cs, int n, const void* const* rh
                 continue;
             }
             CKL(blas_acc(c->x[1], ss[i].xp, c->inner[P].x, c->n5, c->g.Ls, c->scal, 0, st), "acc");
+            ss[i].x_zero = false;
         }
     }
     cudaGraphExecDestroy(exec);
@@ -1101,6 +1115,11 @@ const char* eofa_last_error(const eofa_ctx* ctx) { return ctx ? ctx->err.c_str()
 int eofa_tile_sites(const eofa_ctx* ctx, int prec, int kind) {
     if (!ctx || prec < 0 || prec > 3 || kind < 0 || kind > 3) return 0;
     return tile_sites(ctx->g.Ls, ctx->tuned[prec] ? ctx->tile[prec][kind] : 0);
+}
+
+int eofa_tile_variant(const eofa_ctx* ctx, int prec, int kind) {
+    if (!ctx || prec < 0 || prec > 3 || kind < 0 || kind > 3) return -1;
+    return ctx->tuned[prec] ? ctx->tile[prec][kind] : 0;
 }
 
 double eofa_hop_bytes(const eofa_ctx* ctx, int prec, int with_local) {
@@ -1553,7 +1572,7 @@ extern "C" eofa_status eofa_train_preconditioner(eofa_ctx* ctx, const void* cons
         if ((s = solve_begin(c, (const double*)sources[j], (const double*)sources[j], o, ss, st))) return s;
         CK(cudaStreamSynchronize(st), "sync");
         if (c->h_scal->store[1] + c->h_scal->store[2] == 0.0) continue;
-        if ((s = outer_residual(c, st))) return s;
+        if ((s = outer_residual(c, ss, st))) return s;
         CKL(blas_copy(EOFA_F32, in.r, 0, c->ro, n5, Ls, 1.0, 0, red(c, FIN_NONE), st), "copy");
         const double tol = opts->solve_tol;
         CKL(scal_init(c->scal, tol * tol, 100000, 0ull, st), "scal_init");
