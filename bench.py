@@ -52,6 +52,13 @@ def workload_desc(inner):
             f"eps={w['eps']}, eo Cayley-form CGNR, {inner} inner / FP64 defect correction to r=1e-10")
 
 
+def config_of(args, ws):
+    """The workload of a bench line (the same for both arms)."""
+    return {"workload": workload_desc(args.inner), "lattice": "16x16x16x32", "Ls": 16,
+            "inner": args.inner, "tol": TOL, "parallelism": f"replicas{ws}",
+            "l2": "working set > L2 (about 1.2 GB of fields); no flush"}
+
+
 def kernel_hash():
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
@@ -147,9 +154,9 @@ def ncu_traffic():
     return d
 
 
-def oracle_sample(iters_per_sample, samples=1):
-    """Time the FP64 CPU oracle's CGNR on the full workload (bounded sample)
-    and scale to seconds per solve with the oracle's recorded iteration count."""
+def oracle_setup():
+    """The FP64 CPU oracle on the full workload, its right-hand side, and the
+    oracle's recorded CGNR iteration count to r=1e-10 (None if not recorded)."""
     import oracle
     from paper_1706_05843_gb300 import inputs as I
     oracle.build()
@@ -161,13 +168,21 @@ def oracle_sample(iters_per_sample, samples=1):
     n_iter = None
     if os.path.exists(counts):
         n_iter = json.load(open(counts)).get(w["name"], {}).get("iters")
-    times = []
-    for _ in range(samples):
-        t0 = time.perf_counter()
-        _, st = o.solve_h(phi, tol=1e-300, maxit=iters_per_sample)
-        times.append((time.perf_counter() - t0) / max(st.iters, 1))
-    per_iter = statistics.median(times)
-    return per_iter, n_iter, oracle.num_threads()
+    return o, phi, n_iter, oracle.num_threads()
+
+
+def oracle_time(o, phi, iters):
+    """Seconds per oracle CGNR iteration over a bounded run of `iters`."""
+    t0 = time.perf_counter()
+    _, st = o.solve_h(phi, tol=1e-300, maxit=iters)
+    return (time.perf_counter() - t0) / max(st.iters, 1)
+
+
+def oracle_sample(iters_per_sample):
+    """Time the FP64 CPU oracle's CGNR on the full workload (bounded sample)
+    and scale to seconds per solve with the oracle's recorded iteration count."""
+    o, phi, n_iter, cores = oracle_setup()
+    return oracle_time(o, phi, iters_per_sample), n_iter, cores
 
 
 def _timed(torch, fn):
@@ -274,9 +289,10 @@ def run_reference(args):
     if rank != 0:
         return
     steps, warm = args.steps, args.warmup
+    o, phi, n_iter, cores = oracle_setup()
     per = []
     for i in range(warm + steps):
-        pi, n_iter, cores = oracle_sample(args.ref_iters)
+        pi = oracle_time(o, phi, args.ref_iters)
         if i >= warm:
             per.append(pi)
     per_iter = statistics.median(per)
@@ -290,7 +306,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": val, "unit": "s/solve", "n_gpus": ws,
         "steps": steps, "warmup": warm, "ms_per_step": per_iter * args.ref_iters * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload_desc("FP64 oracle (unpreconditioned)")},
+        "data": "synthetic", "config": config_of(args, ws),
+        "solver": "FP64 CPU oracle: unpreconditioned CGNR on the full-lattice H-form system to r=1e-10",
         "cpu_baseline": {"value": val, "unit": "s/solve", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "s/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -436,9 +453,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.inner != "f64" else "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(args.inner), "lattice": "16x16x16x32", "Ls": 16,
-                   "inner": args.inner, "tol": TOL, "parallelism": f"replicas{ws}",
-                   "l2": "working set > L2 (about 1.2 GB of fields); no flush"},
+        "config": config_of(args, ws),
         "e2e": {"value": e2e_val, "unit": "s/solve", "h2d_bytes_per_step": int(host_rhs.numel() * 16),
                 "d2h_bytes_per_step": int(host_sol.numel() * 16)},
         "gpu_launches": launches * args.steps,
@@ -463,7 +478,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--inner", default="f32", choices=["f64", "f32", "f16", "bf16"])
-    ap.add_argument("--ref-iters", type=int, default=8, help="oracle iterations per CPU sample")
+    ap.add_argument("--ref-iters", type=int, default=4, help="oracle iterations per CPU sample")
     ap.add_argument("--quick", action="store_true", help="skip the other-precision solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--learned", action="store_true",
