@@ -201,7 +201,7 @@ def eofa_solve_batched(ctxs, rhss, sols, opts, stream=None, check=True):
     st = (eofa_solve_stats * n)()
     s = lib().eofa_solve_batched(ca, n, ra, sa, C.byref(opts), st, _stream(stream))
     if check:
-        _check(None, s)
+        _check(ctxs[0] if n else None, s)  # errors are reported on the first context
     return list(st)
 
 

@@ -567,6 +567,61 @@ inline int tile_sites(int Ls, int var) {
     }
 }
 
+// raw link records (rows 0 and 1 in storage precision) are staged with
+// cp.async, 16-byte pieces (8-byte for 16-bit storage)
+template <typename S> struct LinkRaw {
+    static constexpr int BYTES = 12 * (int)sizeof(S);
+    // storage = compute precision: the record lands in rows 0-1 of its
+    // staged link and row 2 is rebuilt in place; 16-bit storage needs a
+    // separate raw buffer
+    static constexpr bool SEP = sizeof(S) != sizeof(typename Traits<S>::R);
+    static constexpr int PAD = SEP ? (BYTES + 15) / 16 * 16 : 0;
+};
+
+__device__ __forceinline__ void stage_cp16(void* dst, const void* src) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void stage_cp8(void* dst, const void* src) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void stage_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// one staged raw link record -> 12 reals of compute precision
+template <typename S, typename R>
+__device__ __forceinline__ void link_from_raw(const unsigned char* raw, R* u) {
+    if constexpr (sizeof(S) == 8) {
+        const double2* p = reinterpret_cast<const double2*>(raw);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const double2 t = p[c];
+            u[2 * c] = t.x;
+            u[2 * c + 1] = t.y;
+        }
+    } else if constexpr (sizeof(S) == 4) {
+        const float4* p = reinterpret_cast<const float4*>(raw);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float4 t = p[c];
+            u[4 * c] = t.x;
+            u[4 * c + 1] = t.y;
+            u[4 * c + 2] = t.z;
+            u[4 * c + 3] = t.w;
+        }
+    } else {
+        const uint2* p = reinterpret_cast<const uint2*>(raw);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) unpack4(p[c], (const S*)nullptr, u + 4 * c);
+    }
+}
+
+// Persistent CTAs: a CTA walks the site blocks blockIdx.x, +gridDim.x, ...
+// While it works on one block, the links and neighbour indices of its next
+// block are already on their way (cp.async into a second staging buffer),
+// so the link latency is off the critical path, and the norm reduction runs
+// once per CTA instead of once per block.
 template <typename S, int LS, int KIND, int VAR>
 __device__ __forceinline__ void hop_body(const HopArgs& a, const SCoef<typename Traits<S>::R>& cf) {
     typedef typename Traits<S>::R R;
@@ -575,6 +630,9 @@ __device__ __forceinline__ void hop_body(const HopArgs& a, const SCoef<typename 
     constexpr int NT = Tile<LS, VAR>::NT;
     constexpr int ST = ShStride<R>::V;
     constexpr int SS = SiteStride<R, LS>::V;
+    constexpr int LK = LinkStride<R>::V;
+    constexpr int NL = NS * 8;  // staged links (and neighbour indices) per block
+    constexpr int RAWB = LinkRaw<S>::PAD;
 
     if (a.done && *a.done) return;
 
@@ -583,165 +641,207 @@ __device__ __forceinline__ void hop_body(const HopArgs& a, const SCoef<typename 
     constexpr bool COLS = ShflTail<KIND, LS>::COLS;  // column phase and its tile buffers
     R* sh = reinterpret_cast<R*>(smem_raw);          // [NS][SS] hop result
     R* sy = sh + (COLS ? NS * SS : 0);                // [NS][SS] local input
+    R* sl = sy + ((KT::HASY && COLS) ? NS * SS : 0);  // [2][NL][LK] links, row 2 rebuilt
+    unsigned char* sraw = reinterpret_cast<unsigned char*>(sl + (KT::HOP ? 2 * NL * LK : 0));  // [2][NL][RAWB]
+    unsigned* snb = reinterpret_cast<unsigned*>(sraw + (KT::HOP ? 2 * NL * RAWB : 0));        // [2][NL]
 
+    const Geom& g = a.g;
     const int tid = threadIdx.x;
     const int il = tid / LS;
     const int s = tid - il * LS;
-    const long xcb = (long)blockIdx.x * NS + il;
-    const bool valid = xcb < a.g.Vh;
     const int rp = il * SS + s * ST;                  // row of the P+ half
     const int rm = il * SS + (LS - 1 - s) * ST + 12;  // row of the P- half
+    const long nblk = ((long)g.Vh + NS - 1) / NS;
 
     // ---------------- phase 0: links and neighbours, once per 4D site ---
     // The 8 links of each site (4 forward from this parity, 4 backward from
-    // the neighbours) are loaded once, their third row rebuilt, and kept in
-    // shared memory for all Ls slices of the site, together with the 8
-    // neighbour indices (bit 31: the hop crosses the time boundary).
-    R* sl = sy + ((KT::HASY && COLS) ? NS * SS : 0);  // [NS][8][LK]
-    constexpr int LK = LinkStride<R>::V;
-    unsigned* snb = reinterpret_cast<unsigned*>(sl + NS * 8 * LK);  // [NS][8]
-    if constexpr (KT::HOP) {
-        const Geom& g = a.g;
-        for (int j = tid; j < NS * 8; j += NT) {
+    // the neighbours) and the 8 neighbour indices (bit 31: the hop crosses
+    // the time boundary) for all Ls slices of the site.  Issue: indices and
+    // cp.async of the raw records; finish: the third row rebuilt.
+    auto stage_issue = [&](long blk, int b) {
+        for (int j = tid; j < NL; j += NT) {
             const int jl = j >> 3, d = j & 7, mu = d & 3;
-            const long jcb = (long)blockIdx.x * NS + jl;
+            const long jcb = blk * NS + jl;
             if (jcb < g.Vh) {
                 int rem = (int)jcb;
                 const int xh = rem % g.Xh; rem /= g.Xh;
                 const int y = rem % g.Y; rem /= g.Y;
                 const int z = rem % g.Z;
                 const int t = rem / g.Z;
-                int cn[4] = {2 * xh + ((a.out_par + y + z + t) & 1), y, z, t};
-                const int dm[4] = {g.X, g.Y, g.Z, g.T};
-                unsigned edge = 0u;
-                if (d < 4) {
-                    edge = (mu == 3 && cn[3] == dm[3] - 1) ? 0x80000000u : 0u;
-                    cn[mu] = (cn[mu] + 1 == dm[mu]) ? 0 : cn[mu] + 1;
+                const int x = 2 * xh + ((a.out_par + y + z + t) & 1);
+                // step in direction mu (forward for d < 4), periodic wrap
+                const int c = mu == 0 ? x : mu == 1 ? y : mu == 2 ? z : t;
+                const int e = mu == 0 ? g.X : mu == 1 ? g.Y : mu == 2 ? g.Z : g.T;
+                const int n = (d < 4) ? (c + 1 == e ? 0 : c + 1) : (c == 0 ? e - 1 : c - 1);
+                const unsigned edge = (mu == 3 && (d < 4 ? t == g.T - 1 : t == 0)) ? 0x80000000u : 0u;
+                const long ncb = ((((long)(mu == 3 ? n : t) * g.Z + (mu == 2 ? n : z)) * g.Y + (mu == 1 ? n : y)) *
+                                      g.X + (mu == 0 ? n : x)) >> 1;
+                snb[b * NL + j] = (unsigned)ncb | edge;
+                const long site = (d < 4) ? jcb : ncb;
+                const unsigned char* src = reinterpret_cast<const unsigned char*>(d < 4 ? a.lk_out : a.lk_in) +
+                                           (site * 4 + mu) * LinkRaw<S>::BYTES;
+                unsigned char* dst = LinkRaw<S>::SEP ? sraw + (b * NL + j) * RAWB
+                                                     : reinterpret_cast<unsigned char*>(sl + (b * NL + j) * LK);
+                if constexpr (sizeof(S) >= 4) {
+#pragma unroll
+                    for (int c = 0; c < LinkRaw<S>::BYTES / 16; ++c) stage_cp16(dst + 16 * c, src + 16 * c);
                 } else {
-                    edge = (mu == 3 && cn[3] == 0) ? 0x80000000u : 0u;
-                    cn[mu] = (cn[mu] == 0) ? dm[mu] - 1 : cn[mu] - 1;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) stage_cp8(dst + 8 * c, src + 8 * c);
                 }
-                const long ncb = ((((long)cn[3] * g.Z + cn[2]) * g.Y + cn[1]) * g.X + cn[0]) >> 1;
-                snb[j] = (unsigned)ncb | edge;
+            }
+        }
+        stage_commit();
+    };
+    auto stage_finish = [&](long blk, int b) {
+        stage_wait();  // this thread's own copies
+        for (int j = tid; j < NL; j += NT) {
+            if (blk * NS + (j >> 3) < g.Vh) {
                 R u[18];
-                if (d < 4) load_link<S, R>(a.lk_out, jcb, mu, u);
-                else load_link<S, R>(a.lk_in, ncb, mu, u);
+                R* dl = sl + (b * NL + j) * LK;
+                if constexpr (LinkRaw<S>::SEP) link_from_raw<S, R>(sraw + (b * NL + j) * RAWB, u);
+                else link_from_raw<S, R>(reinterpret_cast<const unsigned char*>(dl), u);
                 rebuild_row2(u);
 #pragma unroll
-                for (int i = 0; i < 18; ++i) sl[j * LK + i] = u[i];
+                for (int i = 0; i < 18; ++i) dl[i] = u[i];
             }
+        }
+    };
+
+    long blk = blockIdx.x;
+    if constexpr (KT::HOP) {
+        if (blk < nblk) {
+            stage_issue(blk, 0);
+            stage_finish(blk, 0);
         }
         __syncthreads();
     }
 
-    // ---------------- phase 1: hop and staging --------------------------
-    R o[24];    // the output spinor of this thread's 5D site
-    R acc[24];  // its hop result (zero for padding sites)
-#pragma unroll
-    for (int i = 0; i < 24; ++i) acc[i] = (R)0;
-    if (valid) {
+    R nn = (R)0;
+    for (int it = 0; blk < nblk; ++it, blk += gridDim.x) {
+        const int cur = it & 1;
+        const long nxt = blk + gridDim.x;
         if constexpr (KT::HOP) {
-            constexpr int FS = KT::DAG ? +1 : -1;  // forward projector 1 + FS gamma
+            if (nxt < nblk) stage_issue(nxt, cur ^ 1);
+        }
+        const R* slc = sl + cur * NL * LK;
+        const unsigned* snc = snb + cur * NL;
+        const long xcb = blk * NS + il;
+        const bool valid = xcb < g.Vh;
+
+        // ---------------- phase 1: hop and staging ----------------------
+        R o[24];    // the output spinor of this thread's 5D site
+        R acc[24];  // its hop result (zero for padding sites)
 #pragma unroll
-            for (int mu = 0; mu < 4; ++mu) {
+        for (int i = 0; i < 24; ++i) acc[i] = (R)0;
+        if (valid) {
+            if constexpr (KT::HOP) {
+                constexpr int FS = KT::DAG ? +1 : -1;  // forward projector 1 + FS gamma
 #pragma unroll
-                for (int dir = 0; dir < 2; ++dir) {
-                    const unsigned nb = snb[il * 8 + dir * 4 + mu];
-                    const long ncb = (long)(nb & 0x7fffffffu);
-                    const R ph = (mu == 3 && (nb >> 31)) ? (R)a.g.tbc : (R)1;
-                    R p[24];
-                    load_sp<S, R>(a.in, a.in_nrm, ncb, s, LS, p);
-                    if constexpr (KT::PRE) {
-                        // chi = psi + (c5/b5) L psi (the b5 factor is applied in phase 2)
-                        R q[12];
-                        const int sm = (s == 0) ? LS - 1 : s - 1;
-                        const R fu = (s == 0) ? -cf.mzb : cf.zb;
-                        load_half<S, R>(a.in, a.in_nrm, ncb, sm, LS, 0, q);
+                for (int mu = 0; mu < 4; ++mu) {
 #pragma unroll
-                        for (int i = 0; i < 12; ++i) p[i] += fu * q[i];
-                        const int sp = (s == LS - 1) ? 0 : s + 1;
-                        const R fd = (s == LS - 1) ? -cf.mzb : cf.zb;
-                        load_half<S, R>(a.in, a.in_nrm, ncb, sp, LS, 1, q);
+                    for (int dir = 0; dir < 2; ++dir) {
+                        const unsigned nb = snc[il * 8 + dir * 4 + mu];
+                        const long ncb = (long)(nb & 0x7fffffffu);
+                        const R ph = (mu == 3 && (nb >> 31)) ? (R)g.tbc : (R)1;
+                        R p[24];
+                        load_sp<S, R>(a.in, a.in_nrm, ncb, s, LS, p);
+                        if constexpr (KT::PRE) {
+                            // chi = psi + (c5/b5) L psi (the b5 factor is applied in phase 2)
+                            R q[12];
+                            const int sm = (s == 0) ? LS - 1 : s - 1;
+                            const R fu = (s == 0) ? -cf.mzb : cf.zb;
+                            load_half<S, R>(a.in, a.in_nrm, ncb, sm, LS, 0, q);
 #pragma unroll
-                        for (int i = 0; i < 12; ++i) p[12 + i] += fd * q[i];
-                    }
-                    R u[18];
-                    {
-                        const R* src = sl + (il * 8 + dir * 4 + mu) * LK;
+                            for (int i = 0; i < 12; ++i) p[i] += fu * q[i];
+                            const int sp = (s == LS - 1) ? 0 : s + 1;
+                            const R fd = (s == LS - 1) ? -cf.mzb : cf.zb;
+                            load_half<S, R>(a.in, a.in_nrm, ncb, sp, LS, 1, q);
 #pragma unroll
-                        for (int i = 0; i < 18; ++i) u[i] = src[i];
-                    }
-                    if (dir == 0) {
-                        if (mu == 0) hop_dir<R, 0, FS, false>(acc, p, u, ph);
-                        if (mu == 1) hop_dir<R, 1, FS, false>(acc, p, u, ph);
-                        if (mu == 2) hop_dir<R, 2, FS, false>(acc, p, u, ph);
-                        if (mu == 3) hop_dir<R, 3, FS, false>(acc, p, u, ph);
-                    } else {
-                        if (mu == 0) hop_dir<R, 0, -FS, true>(acc, p, u, ph);
-                        if (mu == 1) hop_dir<R, 1, -FS, true>(acc, p, u, ph);
-                        if (mu == 2) hop_dir<R, 2, -FS, true>(acc, p, u, ph);
-                        if (mu == 3) hop_dir<R, 3, -FS, true>(acc, p, u, ph);
+                            for (int i = 0; i < 12; ++i) p[12 + i] += fd * q[i];
+                        }
+                        R u[18];
+                        {
+                            const R* src = slc + (il * 8 + dir * 4 + mu) * LK;
+#pragma unroll
+                            for (int i = 0; i < 18; ++i) u[i] = src[i];
+                        }
+                        if (dir == 0) {
+                            if (mu == 0) hop_dir<R, 0, FS, false>(acc, p, u, ph);
+                            if (mu == 1) hop_dir<R, 1, FS, false>(acc, p, u, ph);
+                            if (mu == 2) hop_dir<R, 2, FS, false>(acc, p, u, ph);
+                            if (mu == 3) hop_dir<R, 3, FS, false>(acc, p, u, ph);
+                        } else {
+                            if (mu == 0) hop_dir<R, 0, -FS, true>(acc, p, u, ph);
+                            if (mu == 1) hop_dir<R, 1, -FS, true>(acc, p, u, ph);
+                            if (mu == 2) hop_dir<R, 2, -FS, true>(acc, p, u, ph);
+                            if (mu == 3) hop_dir<R, 3, -FS, true>(acc, p, u, ph);
+                        }
                     }
                 }
+                if constexpr (KT::PTW) {
+                    // out = [M] y + f h, finished in registers
+                    const R f = ((KIND == KIND_FULL) ? (R)-0.5 : (R)0.5) * (KT::PRE ? cf.b5 : (R)1);
+                    R v[24];
+                    load_sp<S, R>(a.y, a.y_nrm, xcb, s, LS, v);
+                    if constexpr (KIND != KIND_SRC) site_M<S, R, LS>(a.y, a.y_nrm, xcb, s, cf, v);
+#pragma unroll
+                    for (int i = 0; i < 24; ++i) o[i] = v[i] + f * acc[i];
+                } else if constexpr (COLS) {
+                    st_half(sh + rp, acc);
+                    st_half(sh + rm, acc + 12);
+                }
             }
-            if constexpr (KT::PTW) {
-                // out = [M] y + f h, finished in registers
-                const R f = ((KIND == KIND_FULL) ? (R)-0.5 : (R)0.5) * (KT::PRE ? cf.b5 : (R)1);
+            if constexpr (KT::HASY && COLS) {
                 R v[24];
                 load_sp<S, R>(a.y, a.y_nrm, xcb, s, LS, v);
-                if constexpr (KIND != KIND_SRC) site_M<S, R, LS>(a.y, a.y_nrm, xcb, s, cf, v);
-#pragma unroll
-                for (int i = 0; i < 24; ++i) o[i] = v[i] + f * acc[i];
-            } else if constexpr (COLS) {
-                st_half(sh + rp, acc);
-                st_half(sh + rm, acc + 12);
+                st_half(sy + rp, v);
+                st_half(sy + rm, v + 12);
             }
         }
-        if constexpr (KT::HASY && COLS) {
+        if constexpr (SHF) {
+            // out = M^T y + f D~^T h with the slice neighbours from the site's lanes
             R v[24];
-            load_sp<S, R>(a.y, a.y_nrm, xcb, s, LS, v);
-            st_half(sy + rp, v);
-            st_half(sy + rm, v + 12);
-        }
-    }
-    if constexpr (SHF) {
-        // out = M^T y + f D~^T h with the slice neighbours from the site's lanes
-        R v[24];
-        if (valid) {
-            load_sp<S, R>(a.y, a.y_nrm, xcb, s, LS, v);
-        } else {
+            if (valid) {
+                load_sp<S, R>(a.y, a.y_nrm, xcb, s, LS, v);
+            } else {
 #pragma unroll
-            for (int i = 0; i < 24; ++i) v[i] = (R)0;
+                for (int i = 0; i < 24; ++i) v[i] = (R)0;
+            }
+            const R f = (KIND == KIND_FULL_DAG) ? (R)-0.5 : (R)0.5;
+            site_MT_dtT<R, LS>(s, cf, v, acc, f, o);
         }
-        const R f = (KIND == KIND_FULL_DAG) ? (R)-0.5 : (R)0.5;
-        site_MT_dtT<R, LS>(s, cf, v, acc, f, o);
-    }
 
-    // ---------------- phase 2: fifth-dimension program ------------------
-    if constexpr (COLS) {
-        __syncthreads();
-        const R hb = KT::PRE ? cf.b5 : (R)1;  // the b5 of the on-the-fly D~
-        for (int col = tid; col < NS * 12; col += NT) {
-            const int ci = col / 12;
-            const int cc = col - ci * 12;     // spin * 3 + colour
-            const bool shv = cf.has_shift && ((cc >= 6 ? 1 : 0) == cf.cs);
-            column_program<R, LS, KIND, ST>(sh + ci * SS + 2 * cc, sy + ci * SS + 2 * cc, cf, shv, hb);
-        }
-        __syncthreads();
-    }
-
-    // ---------------- phase 3: store + reduction ------------------------
-    R nn = (R)0;
-    if (valid) {
+        // ---------------- phase 2: fifth-dimension program --------------
         if constexpr (COLS) {
-            ld_half(sh + rp, o);
-            ld_half(sh + rm, o + 12);
+            __syncthreads();
+            const R hb = KT::PRE ? cf.b5 : (R)1;  // the b5 of the on-the-fly D~
+            for (int col = tid; col < NS * 12; col += NT) {
+                const int ci = col / 12;
+                const int cc = col - ci * 12;     // spin * 3 + colour
+                const bool shv = cf.has_shift && ((cc >= 6 ? 1 : 0) == cf.cs);
+                column_program<R, LS, KIND, ST>(sh + ci * SS + 2 * cc, sy + ci * SS + 2 * cc, cf, shv, hb);
+            }
+            __syncthreads();
         }
-        store_sp<S, R>(a.out, a.out_nrm, xcb, s, LS, o);
-        if (a.rd.fin != FIN_NONE) {
+
+        // ---------------- phase 3: store ----------------------------------
+        if (valid) {
+            if constexpr (COLS) {
+                ld_half(sh + rp, o);
+                ld_half(sh + rm, o + 12);
+            }
+            store_sp<S, R>(a.out, a.out_nrm, xcb, s, LS, o);
+            if (a.rd.fin != FIN_NONE) {
 #pragma unroll
-            for (int i = 0; i < 24; ++i) nn += o[i] * o[i];
+                for (int i = 0; i < 24; ++i) nn += o[i] * o[i];
+            }
         }
+
+        if constexpr (KT::HOP) {
+            if (nxt < nblk) stage_finish(nxt, cur ^ 1);
+        }
+        __syncthreads();  // next block's links in place; this block's tiles free
     }
     if (a.rd.fin != FIN_NONE) block_reduce_finalize<NT>(nn, a.rd);
 }
@@ -763,8 +863,9 @@ template <typename S, int LS, int K, int VAR = 0>
 constexpr size_t hop_smem_bytes() {
     typedef typename Traits<S>::R R;
     constexpr size_t bufs = ShflTail<K, LS>::COLS ? (1 + (KindTraits<K>::HASY ? 1 : 0)) : 0;
-    return (bufs * (size_t)Tile<LS, VAR>::NS * SiteStride<R, LS>::V +
-            (KindTraits<K>::HOP ? (size_t)Tile<LS, VAR>::NS * 8 * (LinkStride<R>::V + 1) : 0)) * sizeof(R);
+    constexpr size_t NL = (size_t)Tile<LS, VAR>::NS * 8;
+    return bufs * (size_t)Tile<LS, VAR>::NS * SiteStride<R, LS>::V * sizeof(R) +
+           (KindTraits<K>::HOP ? 2 * NL * (LinkStride<R>::V * sizeof(R) + LinkRaw<S>::PAD + sizeof(unsigned)) : 0);
 }
 
 }  // namespace eofa

@@ -18,21 +18,36 @@ static cudaError_t launch_one(const HopArgs& a, const SCoef<typename Traits<S>::
     constexpr int NS = Tile<LS, VAR>::NS;
     constexpr int NT = Tile<LS, VAR>::NT;
     const size_t smem = hop_smem_bytes<S, LS, K, VAR>();
+    static_assert(hop_smem_bytes<S, LS, K, VAR>() <= 232448, "tile exceeds the 227 KB of shared memory per CTA");
     constexpr bool R64 = (VAR & 2) != 0;
-    static bool attr_done = false;  // per instantiation; set before first launch
-    if (!attr_done) {
+    // per instantiation, before its first launch: the shared-memory limit
+    // and the number of CTAs one SM holds (the persistent grid is that many
+    // per SM)
+    static int resident = 0;
+    if (resident == 0) {
         cudaError_t e;
-        if constexpr (R64)
+        if constexpr (R64) {
             e = cudaFuncSetAttribute(hop_kernel_r64<S, LS, K, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem);
-        else
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, hop_kernel_r64<S, LS, K, VAR>, NT,
+                                                                  smem);
+        } else {
             e = cudaFuncSetAttribute(hop_kernel<S, LS, K, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, hop_kernel<S, LS, K, VAR>, NT, smem);
+        }
         if (e != cudaSuccess) return e;
-        attr_done = true;
+        if (resident < 1) resident = 1;
     }
-    const int grid = (a.g.Vh + NS - 1) / NS;
-    if (grid == 0) return cudaSuccess;
+    const long nblk = ((long)a.g.Vh + NS - 1) / NS;
+    if (nblk == 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<long>(nblk, (long)resident * sms);
     if constexpr (R64) hop_kernel_r64<S, LS, K, VAR><<<grid, NT, smem, st>>>(a, c);
     else hop_kernel<S, LS, K, VAR><<<grid, NT, smem, st>>>(a, c);
     return cudaGetLastError();

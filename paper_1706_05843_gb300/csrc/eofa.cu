@@ -387,7 +387,13 @@ eofa_status autotune(eofa_ctx* c, int P, cudaStream_t st) {
                     return even_out ? hop(c, P, k, 0, odd_a, none, even_t, red(c, FIN_NONE), nullptr, st)
                                     : hop(c, P, k, 1, even_t, odd_a, odd_b, red(c, FIN_NONE), nullptr, st);
                 };
-                if ((s = launch())) break;  // warm-up
+                if ((s = launch())) {  // warm-up; a variant the device cannot launch is skipped
+                    if (v == 0) break;
+                    cudaGetLastError();
+                    c->err.clear();
+                    s = EOFA_OK;
+                    continue;
+                }
                 cudaEventRecord(e0, st);
                 for (int r = 0; r < 3 && s == EOFA_OK; ++r) s = launch();
                 cudaEventRecord(e1, st);
@@ -873,9 +879,15 @@ eofa_status solve_batched_impl(eofa_ctx* const* cs, int n, const void* const* rh
     eofa_status s;
     for (int i = 0; i < n; ++i) {
         cs[i]->err.clear();
-        if ((s = solve_begin(cs[i], (const double*)rhs[i], (const double*)sol[i], o, ss[i], st))) return s;
+        if ((s = solve_begin(cs[i], (const double*)rhs[i], (const double*)sol[i], o, ss[i], st))) {
+            if (i > 0) cs[0]->err = "system " + std::to_string(i) + ": " + cs[i]->err;
+            return s;
+        }
     }
-    if (cudaStreamSynchronize(st) != cudaSuccess) return EOFA_ERR_CUDA;
+    {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(cs[0], e, "batched solve start");
+    }
     for (int i = 0; i < n; ++i)
         if ((s = solve_check_rhs(cs[i], (double*)sol[i], ss[i], st))) return s;
     const int P = ss[0].P;
@@ -885,7 +897,10 @@ eofa_status solve_batched_impl(eofa_ctx* const* cs, int n, const void* const* rh
         int active = 0;
         for (int i = 0; i < n; ++i)
             if (!ss[i].finished && (s = outer_residual(cs[i], ss[i], st))) { cudaGraphExecDestroy(exec); return s; }
-        if (cudaStreamSynchronize(st) != cudaSuccess) { cudaGraphExecDestroy(exec); return EOFA_ERR_CUDA; }
+        if (const cudaError_t e = cudaStreamSynchronize(st); e != cudaSuccess) {
+            cudaGraphExecDestroy(exec);
+            return cuda_fail(cs[0], e, "batched outer residual");
+        }
         for (int i = 0; i < n; ++i) {
             if (ss[i].finished) continue;
             if (!outer_decide(cs[i], o, ss[i])) ss[i].finished = true;
@@ -897,10 +912,16 @@ eofa_status solve_batched_impl(eofa_ctx* const* cs, int n, const void* const* rh
             CKL(inner_ctl(c->scal, ss[i].finished ? 1 : 0, std::max(1, ss[i].maxit - ss[i].total), st), "inner_ctl");
         }
         if (active == 0) break;
-        if (cudaGraphLaunch(exec, st) != cudaSuccess) { cudaGraphExecDestroy(exec); return EOFA_ERR_CUDA; }
+        if (const cudaError_t e = cudaGraphLaunch(exec, st); e != cudaSuccess) {
+            cudaGraphExecDestroy(exec);
+            return cuda_fail(cs[0], e, "batched graph launch");
+        }
         for (int i = 0; i < n; ++i)
             if ((s = enqueue_read(cs[i], st))) { cudaGraphExecDestroy(exec); return s; }
-        if (cudaStreamSynchronize(st) != cudaSuccess) { cudaGraphExecDestroy(exec); return EOFA_ERR_CUDA; }
+        if (const cudaError_t e = cudaStreamSynchronize(st); e != cudaSuccess) {
+            cudaGraphExecDestroy(exec);
+            return cuda_fail(cs[0], e, "batched inner solves");
+        }
         for (int i = 0; i < n; ++i) {
             if (ss[i].finished) continue;
             eofa_ctx* c = cs[i];
