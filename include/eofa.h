@@ -111,11 +111,13 @@ typedef struct {
     int status;          /* eofa_status of the solve */
     int outer_iters;     /* defect-correction steps (1 for a plain FP64 solve) */
     int inner_iters;     /* CG iterations summed over all inner solves */
-    int hop_launches;    /* hop kernels timed (kernel_timing = 1), else 0 */
+    int hop_launches;    /* hop kernels timed: every inner-solver hop with kernel_timing = 1;
+                            otherwise a sample, the four hops of one CG iteration per inner
+                            solve, timed by events inside the solver's CUDA graph */
     double true_res;     /* FP64 ||rhs - A sol|| / ||rhs|| on the full lattice */
     double recur_res;    /* last recursively updated residual (relative) */
     double seconds;      /* wall-clock time of the call */
-    double hop_ms;       /* summed hop-kernel time (kernel_timing = 1) */
+    double hop_ms;       /* summed time of the timed hop kernels */
     double hop_bytes;    /* algorithmic bytes moved by the timed hop kernels */
     long kernel_launches;/* kernels this library launched during the call */
     int precond_iters;   /* flexible-GCR steps with the learned preconditioner (precond = 1) */

@@ -56,6 +56,9 @@ struct eofa_ctx {
     bool timing = false;
     std::vector<cudaEvent_t> evs;
     int ev_used = 0;
+    // graph-path timing sample: events around the four hops of the first
+    // iteration of every chunk of the captured CG loop, per precision
+    cudaEvent_t gev[4][8] = {};
     double hop_ms = 0.0;
     int hop_launches = 0;
     double hop_bytes = 0.0;
@@ -68,6 +71,7 @@ struct eofa_ctx {
     // device-driven CG loops, one per inner precision
     cudaStream_t cap = nullptr;
     cudaGraphExec_t cg_exec[4] = {};
+    cudaGraphExec_t cg_first[4] = {};  // the first CG iteration, with timing events
     // learned preconditioner: weights, activations of all Ls slices on the
     // full lattice, flexible-GCR vectors (FP32, odd parity), second
     // reduction buffers for complex inner products
@@ -431,18 +435,48 @@ double since(Clock::time_point t0) {
 // inner.r, solution in inner.x; stops at |r|^2 <= tol^2 (source norm 1).
 // one CGNR iteration on the Schur complement (6 launches); every kernel
 // returns at once when the device flag scal->done is set
-eofa_status cg_iteration(eofa_ctx* c, int P, cudaStream_t st, bool timed) {
+// ev (may be NULL): 8 events recorded around the four hop launches
+eofa_status cg_iteration(eofa_ctx* c, int P, cudaStream_t st, bool timed, cudaEvent_t* ev = nullptr) {
     Inner& in = c->inner[P];
     const int xp = P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
     const int* done = &c->scal->done;
     const VecRef none{};
     eofa_status s;
-    if ((s = hop(c, P, KIND_EO_MINV, 0, in.p, none, in.t, red(c, FIN_NONE), done, st, timed))) return s;
-    if ((s = hop(c, P, KIND_OE_SCHUR, 1, in.t, in.p, in.q, red(c, FIN_ALPHA), done, st, timed))) return s;
+    auto mark = [&](int i) -> eofa_status {
+        // External: under stream capture this becomes an event record node
+        // (a plain record would only mark a capture dependency)
+        if (ev) CK(cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal), "cudaEventRecordWithFlags");
+        return EOFA_OK;
+    };
+    if ((s = mark(0)) || (s = hop(c, P, KIND_EO_MINV, 0, in.p, none, in.t, red(c, FIN_NONE), done, st, timed)) ||
+        (s = mark(1)))
+        return s;
+    if ((s = mark(2)) || (s = hop(c, P, KIND_OE_SCHUR, 1, in.t, in.p, in.q, red(c, FIN_ALPHA), done, st, timed)) ||
+        (s = mark(3)))
+        return s;
     CKL(blas_cg_r(P, in.q, in.r, c->n5, c->g.Ls, red(c, FIN_RR), done, st), "cg_r");
-    if ((s = hop(c, P, KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), done, st, timed))) return s;
-    if ((s = hop(c, P, KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_BETA), done, st, timed))) return s;
+    if ((s = mark(4)) || (s = hop(c, P, KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), done, st, timed)) ||
+        (s = mark(5)))
+        return s;
+    if ((s = mark(6)) ||
+        (s = hop(c, P, KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_BETA), done, st, timed)) ||
+        (s = mark(7)))
+        return s;
     CKL(blas_cg_px(P, xp, in.x, in.p, in.z, c->n5, c->g.Ls, red(c, FIN_STOP), st), "cg_px");
+    return EOFA_OK;
+}
+
+// After a graph-path inner solve: the four hop launches of its first
+// iteration (their own small graph, with events; an iteration that always
+// runs) are added to the timing totals.
+eofa_status fold_graph_sample(eofa_ctx* c, int P) {
+    for (int j = 0; j < 4; ++j) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->gev[P][2 * j], c->gev[P][2 * j + 1]), "cudaEventElapsedTime");
+        c->hop_ms += ms;
+        c->hop_launches += 1;
+        c->hop_bytes += hop_bytes_of(c, P, j == 1 || j == 3);
+    }
     return EOFA_OK;
 }
 
@@ -455,6 +489,8 @@ constexpr int kChunk = 16;  // iterations per graph body / per host check
 eofa_status build_cg_graph(eofa_ctx* c, int P) {
     if (c->cg_exec[P]) return EOFA_OK;
     if (!c->cap) CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    for (int i = 0; i < 8; ++i)
+        if (!c->gev[P][i]) CK(cudaEventCreate(&c->gev[P][i]), "cudaEventCreate");
     cudaGraph_t g = nullptr;
     CK(cudaGraphCreate(&g, 0), "cudaGraphCreate");
     cudaGraphConditionalHandle h;
@@ -498,6 +534,28 @@ eofa_status build_cg_graph(eofa_ctx* c, int P) {
         }
     }
     cudaGraphDestroy(g);
+    if (s != EOFA_OK) return s;
+    // the first iteration of every inner solve runs as its own small graph
+    // with events around its four hop launches: the timing sample
+    cudaGraph_t g1 = nullptr;
+    e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
+    s = cg_iteration(c, P, c->cap, false, c->gev[P]);
+    e2 = cudaStreamEndCapture(c->cap, &g1);
+    c->launches = launches0;
+    if (s == EOFA_OK && e2 != cudaSuccess) s = cuda_fail(c, e2, "cudaStreamEndCapture");
+    if (s == EOFA_OK) {
+        e = cudaGraphInstantiate(&c->cg_first[P], g1, 0);
+        if (e != cudaSuccess) {
+            c->cg_first[P] = nullptr;
+            s = cuda_fail(c, e, "cudaGraphInstantiate");
+        }
+    }
+    if (g1) cudaGraphDestroy(g1);
+    if (s != EOFA_OK && c->cg_exec[P]) {
+        cudaGraphExecDestroy(c->cg_exec[P]);
+        c->cg_exec[P] = nullptr;
+    }
     return s;
 }
 
@@ -525,12 +583,14 @@ eofa_status run_cgnr(eofa_ctx* c, int P, double tol, int maxit, int* iters, doub
     *iters = 0;
     if (!c->timing) {
         if ((s = build_cg_graph(c, P))) return s;
+        CK(cudaGraphLaunch(c->cg_first[P], st), "cudaGraphLaunch");
         CK(cudaGraphLaunch(c->cg_exec[P], st), "cudaGraphLaunch");
         if ((s = read_scal(c, st))) return s;
         const DevScal& h = *c->h_scal;
         *iters = h.iters;
         *rr_out = h.rr;
-        c->launches += (long)(6 * kChunk + 1) * ((h.iters + kChunk - 1) / kChunk + (h.iters == 0 ? 1 : 0));
+        if ((s = fold_graph_sample(c, P))) return s;
+        c->launches += 6 + (long)(6 * kChunk + 1) * std::max(1, (h.iters - 1 + kChunk - 1) / kChunk);
         if (h.nonfinite) return fail(c, EOFA_ERR_NONFINITE, "NaN or Inf in the inner CG reductions");
         if (h.done) return EOFA_OK;
         if (h.timed_out) return fail(c, EOFA_ERR_TIMEOUT, "solve exceeded timeout_ms");
@@ -556,10 +616,14 @@ eofa_status run_cgnr(eofa_ctx* c, int P, double tol, int maxit, int* iters, doub
 eofa_status run_fgcr(eofa_ctx* c, double tol, int maxit, int* iters, cudaStream_t st, Clock::time_point t0,
                      long timeout_ms);
 
+// Inner targets of the defect correction, per storage precision: the
+// smallest that the inner CG still reaches reliably; 2e-6 lets two FP32
+// inner solves reach 1e-10 (measured on the 16^3x32, Ls=16 workload:
+// 2 outer steps at 2e-6 against 3 at 1e-5, same total inner iterations).
 double default_inner_tol(int P) {
     switch (P) {
-        case EOFA_F32: return 1e-5;
-        case EOFA_F16: return 2e-3;
+        case EOFA_F32: return 2e-6;
+        case EOFA_F16: return 1e-3;
         case EOFA_BF16: return 1e-2;
         default: return 0.0;
     }
@@ -1109,8 +1173,13 @@ void eofa_destroy(eofa_ctx* ctx) {
     if (!ctx) return;
     for (void* p : ctx->allocs) cudaFree(p);
     for (cudaEvent_t e : ctx->evs) cudaEventDestroy(e);
-    for (int i = 0; i < 4; ++i)
+    for (auto& row : ctx->gev)
+        for (cudaEvent_t e : row)
+            if (e) cudaEventDestroy(e);
+    for (int i = 0; i < 4; ++i) {
         if (ctx->cg_exec[i]) cudaGraphExecDestroy(ctx->cg_exec[i]);
+        if (ctx->cg_first[i]) cudaGraphExecDestroy(ctx->cg_first[i]);
+    }
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
     delete ctx;

@@ -117,6 +117,23 @@ def test_solve_with_guess_and_zero_rhs(env):
     s.close()
 
 
+def test_hop_timing_stats(env):
+    """Both timing modes report hop launches, time and algorithmic bytes: the
+    graph path a sample of four launches per inner solve, kernel timing every
+    inner-solver hop launch; the solutions agree."""
+    torch, s, o = setup(env, CASES[0])
+    phi = torch.from_numpy(I.gaussian_fermion(CASES[0][0], CASES[0][1], 1001)).cuda()
+    from paper_1706_05843_gb300 import binding as B
+    psi_g, st_g = s.solve(phi, tol=1e-10, inner="f32")
+    psi_t, st_t = s.solve(phi, tol=1e-10, inner="f32", kernel_timing=True)
+    per = B.lib().eofa_hop_bytes(s.ctx, 1, 0) + B.lib().eofa_hop_bytes(s.ctx, 1, 1)
+    assert st_g.hop_launches == 4 * st_g.outer_iters and st_g.hop_ms > 0
+    assert abs(st_g.hop_bytes - per * 2 * st_g.outer_iters) <= 1e-6 * st_g.hop_bytes
+    assert st_t.hop_launches >= 4 * st_t.inner_iters and st_t.hop_ms > 0
+    assert rel(psi_g.cpu().numpy(), psi_t.cpu().numpy()) < 1e-8
+    s.close()
+
+
 def test_not_converged_status(env):
     torch, s, o = setup(env, CASES[0])
     from paper_1706_05843_gb300 import binding as B
