@@ -372,7 +372,7 @@ def run_ours(args):
     for _ in range(args.steps):
         # the production path (graph-captured CG loop); the solver times a
         # sample of its hop launches with events recorded inside the graph
-        _, st = solver.solve(rhs, out=sol, **opts)
+        _, st = solver.solve(rhs, out=sol, kernel_timing=args.host_loop, **opts)
         stats.append(st.as_dict())
     e1.record(stream)
     torch.cuda.synchronize()
@@ -490,6 +490,9 @@ def main():
                     help="also train the learned preconditioner and time it at 32^3x64 Ls=12 (minutes)")
     ap.add_argument("--profile", action="store_true",
                     help="one solve capped at 16 inner iterations, nothing else (for ncu captures)")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="timed solves with the host-driven CG loop and every hop timed (ncu launch lists: "
+                         "ncu does not profile the kernels inside the solver's conditional graph nodes)")
     args = ap.parse_args()
     if args.profile:
         args.quick, args.no_cpu, args.steps, args.warmup = True, True, 1, 0

@@ -13,6 +13,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <array>
 #include <cstring>
 #include <map>
@@ -347,6 +348,16 @@ std::map<std::array<long, 5>, int> g_tune_cache;  // (prec, Ls, X*Y, Z*T, kind) 
 
 eofa_status autotune(eofa_ctx* c, int P, cudaStream_t st) {
     if (c->tuned[P]) return EOFA_OK;
+    // EOFA_TILE_VARIANT=v fixes every inner-solver hop kind to variant v
+    // (reproducible profiles); variants FP64 arithmetic lacks fall back to v & 1
+    if (const char* fv = std::getenv("EOFA_TILE_VARIANT")) {
+        const int v = std::atoi(fv);
+        if (v >= 0 && v <= 3) {
+            for (int k = 0; k < 4; ++k) c->tile[P][k] = (P == EOFA_F64) ? (v & 1) : v;
+            c->tuned[P] = true;
+            return EOFA_OK;
+        }
+    }
     const Geom& g = c->g;
     bool all = true;
     {
