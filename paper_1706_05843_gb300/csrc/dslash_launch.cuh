@@ -25,6 +25,11 @@ static cudaError_t launch_one(const HopArgs& a, const SCoef<typename Traits<S>::
     // per SM)
     static int resident = 0;
     if (resident == 0) {
+        // the one-time set-up must not run inside a stream capture (the
+        // drivers launch every kernel once before they capture it)
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+            return cudaErrorStreamCaptureUnsupported;
         cudaError_t e;
         if constexpr (R64) {
             e = cudaFuncSetAttribute(hop_kernel_r64<S, LS, K, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,

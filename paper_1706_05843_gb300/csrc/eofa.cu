@@ -349,18 +349,17 @@ std::map<std::array<long, 5>, int> g_tune_cache;  // (prec, Ls, X*Y, Z*T, kind) 
 eofa_status autotune(eofa_ctx* c, int P, cudaStream_t st) {
     if (c->tuned[P]) return EOFA_OK;
     // EOFA_TILE_VARIANT=v fixes every inner-solver hop kind to variant v
-    // (reproducible profiles); variants FP64 arithmetic lacks fall back to v & 1
+    // (reproducible profiles); variants FP64 arithmetic lacks fall back to
+    // v & 1.  The kernels are still launched once here, before any graph
+    // capture needs them.
+    int forced = -1;
     if (const char* fv = std::getenv("EOFA_TILE_VARIANT")) {
         const int v = std::atoi(fv);
-        if (v >= 0 && v <= 3) {
-            for (int k = 0; k < 4; ++k) c->tile[P][k] = (P == EOFA_F64) ? (v & 1) : v;
-            c->tuned[P] = true;
-            return EOFA_OK;
-        }
+        if (v >= 0 && v <= 3) forced = (P == EOFA_F64) ? (v & 1) : v;
     }
     const Geom& g = c->g;
-    bool all = true;
-    {
+    bool all = forced < 0;
+    if (forced < 0) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         for (int k = 0; k < 4; ++k) {
             auto it = g_tune_cache.find({P, g.Ls, (long)g.X * g.Y, (long)g.Z * g.T, k});
@@ -394,8 +393,9 @@ eofa_status autotune(eofa_ctx* c, int P, cudaStream_t st) {
         const int nvar = (P == EOFA_F64) ? 2 : 4;  // register-capped variants for FP32 arithmetic
         float best[4] = {1e30f, 1e30f, 1e30f, 1e30f};
         // three interleaved rounds; each variant keeps its fastest round
-        for (int round = 0; round < 3 && s == EOFA_OK; ++round) {
+        for (int round = 0; round < (forced < 0 ? 3 : 1) && s == EOFA_OK; ++round) {
             for (int v = 0; v < nvar && s == EOFA_OK; ++v) {
+                if (forced >= 0 && v != forced) continue;
                 c->tuned[P] = true;
                 c->tile[P][k] = v;
                 auto launch = [&]() {
@@ -403,7 +403,7 @@ eofa_status autotune(eofa_ctx* c, int P, cudaStream_t st) {
                                     : hop(c, P, k, 1, even_t, odd_a, odd_b, red(c, FIN_NONE), nullptr, st);
                 };
                 if ((s = launch())) {  // warm-up; a variant the device cannot launch is skipped
-                    if (v == 0) break;
+                    if (v == 0 || forced >= 0) break;
                     cudaGetLastError();
                     c->err.clear();
                     s = EOFA_OK;
@@ -421,7 +421,7 @@ eofa_status autotune(eofa_ctx* c, int P, cudaStream_t st) {
         int best_v = 0;
         for (int v = 1; v < nvar; ++v)
             if (best[v] < best[best_v]) best_v = v;
-        c->tile[P][k] = best_v;
+        c->tile[P][k] = forced >= 0 ? forced : best_v;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -446,7 +446,11 @@ double since(Clock::time_point t0) {
 // inner.r, solution in inner.x; stops at |r|^2 <= tol^2 (source norm 1).
 // one CGNR iteration on the Schur complement (6 launches); every kernel
 // returns at once when the device flag scal->done is set
-// ev (may be NULL): 8 events recorded around the four hop launches
+// One CGNR iteration on the Schur complement (6 launches; every kernel
+// returns at once when scal->done is set): q = S p (|q|^2 -> alpha),
+// r -= alpha q (|r|^2: convergence), z = S^dag r (|z|^2 -> beta), then
+// x += alpha p, p = z + beta p.
+// ev (may be NULL): 8 events recorded around the four hop launches.
 eofa_status cg_iteration(eofa_ctx* c, int P, cudaStream_t st, bool timed, cudaEvent_t* ev = nullptr) {
     Inner& in = c->inner[P];
     const int xp = P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
@@ -474,6 +478,20 @@ eofa_status cg_iteration(eofa_ctx* c, int P, cudaStream_t st, bool timed, cudaEv
         (s = mark(7)))
         return s;
     CKL(blas_cg_px(P, xp, in.x, in.p, in.z, c->n5, c->g.Ls, red(c, FIN_STOP), st), "cg_px");
+    return EOFA_OK;
+}
+
+// Start of an inner CGNR from x = 0 on the source in inner.r (scal already
+// initialised): z = S^dag r (|z|^2 -> zz), p = z.
+eofa_status cg_start(eofa_ctx* c, int P, const int* done, cudaStream_t st) {
+    Inner& in = c->inner[P];
+    const int xp = P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
+    const VecRef none{};
+    eofa_status s;
+    CKL(blas_zero(xp, in.x, c->n5, c->g.Ls, st), "blas_zero");
+    if ((s = hop(c, P, KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), done, st))) return s;
+    if ((s = hop(c, P, KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_ZZ), done, st))) return s;
+    CKL(blas_copy(P, in.p, P, in.z, c->n5, c->g.Ls, 1.0, -1, red(c, FIN_NONE), st), "blas_copy");
     return EOFA_OK;
 }
 
@@ -577,9 +595,6 @@ eofa_status build_cg_graph(eofa_ctx* c, int P) {
 // around every hop kernel.
 eofa_status run_cgnr(eofa_ctx* c, int P, double tol, int maxit, int* iters, double* rr_out, cudaStream_t st,
                      Clock::time_point t0, long timeout_ms) {
-    Inner& in = c->inner[P];
-    const int xp = P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
-    const VecRef none{};
     eofa_status s;
     double left_ms = 0.0;
     if (timeout_ms > 0) {
@@ -587,10 +602,7 @@ eofa_status run_cgnr(eofa_ctx* c, int P, double tol, int maxit, int* iters, doub
         if (left_ms <= 0.0) return fail(c, EOFA_ERR_TIMEOUT, "solve exceeded timeout_ms");
     }
     CKL(scal_init(c->scal, tol * tol, maxit, (unsigned long long)(left_ms * 1e6), st), "scal_init");
-    CKL(blas_zero(xp, in.x, c->n5, c->g.Ls, st), "blas_zero");
-    if ((s = hop(c, P, KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), nullptr, st))) return s;
-    if ((s = hop(c, P, KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_ZZ), nullptr, st))) return s;
-    CKL(blas_copy(P, in.p, P, in.z, c->n5, c->g.Ls, 1.0, -1, red(c, FIN_NONE), st), "blas_copy");
+    if ((s = cg_start(c, P, nullptr, st))) return s;
     *iters = 0;
     if (!c->timing) {
         if ((s = build_cg_graph(c, P))) return s;
@@ -891,17 +903,9 @@ eofa_status build_batch_graph(eofa_ctx* const* cs, int n, int P, double tol, dou
     s = capture_branches([&](int i, cudaStream_t st) -> eofa_status {
         eofa_ctx* ci = cs[i];
         Inner& in = ci->inner[P];
-        const int xp = P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
-        const VecRef none{};
-        eofa_status r;
         CK(inner_init(ci->scal, tol, floor_tol, st), "inner_init");
         CK(blas_copy(P, in.r, 0, ci->ro, ci->n5, ci->g.Ls, 1.0, 0, red(ci, FIN_NONE), st), "copy");
-        CK(blas_zero(xp, in.x, ci->n5, ci->g.Ls, st), "zero");
-        const int* done = &ci->scal->done;
-        if ((r = hop(ci, P, KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(ci, FIN_NONE), done, st))) return r;
-        if ((r = hop(ci, P, KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(ci, FIN_ZZ), done, st))) return r;
-        CK(blas_copy(P, in.p, P, in.z, ci->n5, ci->g.Ls, 1.0, -1, red(ci, FIN_NONE), st), "copy");
-        return EOFA_OK;
+        return cg_start(ci, P, &ci->scal->done, st);
     });
     cudaError_t e2 = cudaStreamEndCapture(str[n], &pro);
     if (s == EOFA_OK && e2 != cudaSuccess) s = cuda_fail(c, e2, "end capture");
@@ -1677,10 +1681,7 @@ extern "C" eofa_status eofa_train_preconditioner(eofa_ctx* ctx, const void* cons
         CKL(blas_copy(EOFA_F32, in.r, 0, c->ro, n5, Ls, 1.0, 0, red(c, FIN_NONE), st), "copy");
         const double tol = opts->solve_tol;
         CKL(scal_init(c->scal, tol * tol, 100000, 0ull, st), "scal_init");
-        CKL(blas_zero(EOFA_F32, in.x, n5, Ls, st), "zero");
-        if ((s = hop(c, EOFA_F32, KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), nullptr, st))) return s;
-        if ((s = hop(c, EOFA_F32, KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_ZZ), nullptr, st))) return s;
-        CKL(blas_copy(EOFA_F32, in.p, EOFA_F32, in.z, n5, Ls, 1.0, -1, red(c, FIN_NONE), st), "copy");
+        if ((s = cg_start(c, EOFA_F32, nullptr, st))) return s;
         int ns = 1;  // snapshot 0 is the zero start vector
         CK(cudaMemsetAsync(snap[0].d, 0, sizeof(float) * n5 * 24, st), "memset");
         for (;;) {
