@@ -280,8 +280,9 @@ double eofa_hop_bytes(const eofa_ctx *ctx, int prec, int with_local);
 int eofa_tile_sites(const eofa_ctx *ctx, int prec, int kind);
 
 /* The tile variant chosen for the same kernel: bit 0 set for the
- * alternative CTA shape, bit 1 set when the kernel is compiled for 64
- * registers per thread (more resident warps; FP32 arithmetic only).
+ * alternative CTA shape, bit 1 set when the kernel is compiled with a
+ * register cap (about 72 per thread: more resident warps; FP32 arithmetic
+ * only).
  * 0 before the first solve in that precision, -1 for invalid arguments.
  * The environment variable EOFA_TILE_VARIANT=0..3, read when a context
  * first tunes a precision, replaces the timing by that fixed variant. */

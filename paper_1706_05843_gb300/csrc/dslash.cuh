@@ -539,9 +539,10 @@ template <> struct LinkStride<double> { static constexpr int V = 18; };
 
 // CTA tile: NS 4D sites x Ls slices, one thread per 5D site.  Bit 0 of the
 // variant picks the shape: 0 the default, 1 twice the sites (half for
-// Ls = 12).  Bit 1 asks for 64 registers per thread (more resident warps,
-// a few spilled values) and applies to FP32 arithmetic only.  The
-// autotuner times the variants for the inner-solver kinds.
+// Ls = 12).  Bit 1 caps the registers at about 72 per thread (one more
+// resident CTA of 128 threads than the compiler's own choice of 80, a few
+// spilled values) and applies to FP32 arithmetic only.  The autotuner
+// times the variants for the inner-solver kinds.
 template <int LS, int VAR = 0> struct Tile {
     static constexpr int NS0 = (LS >= 16) ? 8 : (LS == 12 ? 16 : 128 / LS);
     static constexpr int NS = (VAR & 1) == 0 ? NS0 : (LS == 12 ? NS0 / 2 : NS0 * 2);
@@ -551,8 +552,8 @@ template <int LS, int VAR = 0> struct Tile {
 template <typename S> constexpr int kTileVariants = sizeof(typename Traits<S>::R) == 4 ? 4 : 2;
 
 // the register-capped variants ask for this many resident CTAs per SM
-template <int LS, int VAR> struct MinBlocks64 {
-    static constexpr int V = 65536 / (64 * Tile<LS, VAR>::NT);
+template <int LS, int VAR> struct MinBlocksCap {
+    static constexpr int V = 65536 / (72 * Tile<LS, VAR>::NT);
 };
 
 // sites per CTA of a tile variant (for reports)
@@ -852,10 +853,10 @@ __global__ void __launch_bounds__(Tile<LS, VAR>::NT) hop_kernel(const HopArgs a,
     hop_body<S, LS, KIND, VAR>(a, cf);
 }
 
-// ... and with 64 registers per thread (variants 2, 3; FP32 arithmetic)
+// ... and with capped registers (variants 2, 3; FP32 arithmetic)
 template <typename S, int LS, int KIND, int VAR>
-__global__ void __launch_bounds__(Tile<LS, VAR>::NT, MinBlocks64<LS, VAR>::V)
-    hop_kernel_r64(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
+__global__ void __launch_bounds__(Tile<LS, VAR>::NT, MinBlocksCap<LS, VAR>::V)
+    hop_kernel_rc(const HopArgs a, const SCoef<typename Traits<S>::R> cf) {
     hop_body<S, LS, KIND, VAR>(a, cf);
 }
 

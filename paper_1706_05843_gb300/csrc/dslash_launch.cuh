@@ -4,7 +4,7 @@
 // dslash_<prec>_outer.cu (the FP64/FP32 outer-solver kinds), so the kernel
 // instantiations compile as separate translation units.  The inner kinds
 // exist in every tile variant the autotuner times (two CTA shapes, and for
-// FP32 arithmetic each with and without a 64-register cap); the others in
+// FP32 arithmetic each with and without a register cap); the others in
 // the default variant only.
 #pragma once
 
@@ -19,7 +19,7 @@ static cudaError_t launch_one(const HopArgs& a, const SCoef<typename Traits<S>::
     constexpr int NT = Tile<LS, VAR>::NT;
     const size_t smem = hop_smem_bytes<S, LS, K, VAR>();
     static_assert(hop_smem_bytes<S, LS, K, VAR>() <= 232448, "tile exceeds the 227 KB of shared memory per CTA");
-    constexpr bool R64 = (VAR & 2) != 0;
+    constexpr bool RCAP = (VAR & 2) != 0;
     // per instantiation, before its first launch: the shared-memory limit
     // and the number of CTAs one SM holds (the persistent grid is that many
     // per SM)
@@ -31,11 +31,11 @@ static cudaError_t launch_one(const HopArgs& a, const SCoef<typename Traits<S>::
         if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
             return cudaErrorStreamCaptureUnsupported;
         cudaError_t e;
-        if constexpr (R64) {
-            e = cudaFuncSetAttribute(hop_kernel_r64<S, LS, K, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if constexpr (RCAP) {
+            e = cudaFuncSetAttribute(hop_kernel_rc<S, LS, K, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem);
             if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, hop_kernel_r64<S, LS, K, VAR>, NT,
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, hop_kernel_rc<S, LS, K, VAR>, NT,
                                                                   smem);
         } else {
             e = cudaFuncSetAttribute(hop_kernel<S, LS, K, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -53,7 +53,7 @@ static cudaError_t launch_one(const HopArgs& a, const SCoef<typename Traits<S>::
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<long>(nblk, (long)resident * sms);
-    if constexpr (R64) hop_kernel_r64<S, LS, K, VAR><<<grid, NT, smem, st>>>(a, c);
+    if constexpr (RCAP) hop_kernel_rc<S, LS, K, VAR><<<grid, NT, smem, st>>>(a, c);
     else hop_kernel<S, LS, K, VAR><<<grid, NT, smem, st>>>(a, c);
     return cudaGetLastError();
 }
