@@ -409,6 +409,7 @@ eofa_status autotune(eofa_ctx* c, int P, cudaStream_t st) {
                     s = EOFA_OK;
                     continue;
                 }
+                if (forced >= 0) continue;  // fixed variant: launched once, no timing
                 cudaEventRecord(e0, st);
                 for (int r = 0; r < 3 && s == EOFA_OK; ++r) s = launch();
                 cudaEventRecord(e1, st);
