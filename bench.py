@@ -421,6 +421,22 @@ def run_ours(args):
 
     workloads = {}
     if rank == 0 and not args.quick:
+        # the paper's comparison (Sec. V.B): even-odd on the unpreconditioned
+        # system with the dense Ls x Ls site block, same outer loop and inner precision
+        solver.solve(rhs, out=sol, tol=TOL, inner=args.inner, method=1, check=False)  # set-up and capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st = solver.solve(rhs, out=sol, tol=TOL, inner=args.inner, method=1, check=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        workloads["dense_vs_cayley"] = {
+            "inner": args.inner,
+            "dense": {"s_per_solve": dt, "inner_iters": st.inner_iters, "outer": st.outer_iters,
+                      "true_res": st.true_res, "status": st.status,
+                      "hop_GBps": st.hop_bytes / (st.hop_ms * 1e-3) / 1e9 if st.hop_ms else None},
+            "cayley": {"s_per_solve": value, "inner_iters": stats[-1]["inner_iters"],
+                       "outer": stats[-1]["outer_iters"]},
+            "cayley_speedup": dt / value if value else None}
         solver.close()
         workloads["batched_16rhs_uneven"] = run_batched(B, I, torch, dev)
         workloads["24^3x64_Ls12_4rhs"] = run_multi_rhs(B, I, torch, dev)

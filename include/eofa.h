@@ -102,7 +102,11 @@ typedef struct {
     int use_guess;       /* 1: sol holds an initial guess on entry */
     int rhs_form;        /* 0: H form, rhs = phi, sol = psi.  1: K form, rhs = b, sol = psi' (K psi' = b) */
     int kernel_timing;   /* 1: time every hop kernel with CUDA events (no graph capture) */
-    int pad_;
+    int method;          /* inner operator.  0: the Cayley form (right preconditioning by
+                            D~(m1)^-1, O(Ls) site-diagonal inverse, App. B).  1: even-odd
+                            on Eq. (non_hermit_sys) directly, with the dense Ls x Ls inverse
+                            of its site-diagonal block (the "dense" scheme the paper compares
+                            against, Sec. V.B); same outer loop, for comparison */
     long timeout_ms;     /* 0: none; otherwise wall-clock limit checked between chunks */
 } eofa_solve_opts;
 

@@ -41,7 +41,7 @@ class eofa_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("inner", C.c_int),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int), ("precond", C.c_int),
                 ("use_guess", C.c_int), ("rhs_form", C.c_int), ("kernel_timing", C.c_int),
-                ("pad_", C.c_int), ("timeout_ms", C.c_long)]
+                ("method", C.c_int), ("timeout_ms", C.c_long)]
 
 
 class eofa_solve_stats(C.Structure):
@@ -147,12 +147,12 @@ def make_params(dims, Ls, M5=1.8, b=1.5, c=0.5, m1=0.04, m2=1.0, m3=0.04, beta=-
 
 
 def make_opts(tol=1e-10, inner="f64", inner_tol=0.0, max_iter=0, max_outer=0, use_guess=False,
-              rhs_form=0, kernel_timing=False, timeout_ms=0, precond=0):
+              rhs_form=0, kernel_timing=False, timeout_ms=0, precond=0, method=0):
     o = eofa_solve_opts()
     o.tol, o.inner, o.inner_tol = float(tol), PREC[inner] if isinstance(inner, str) else int(inner), float(inner_tol)
     o.max_iter, o.max_outer, o.precond = int(max_iter), int(max_outer), int(precond)
     o.use_guess, o.rhs_form, o.kernel_timing = int(use_guess), int(rhs_form), int(kernel_timing)
-    o.timeout_ms = int(timeout_ms)
+    o.timeout_ms, o.method = int(timeout_ms), int(method)
     return o
 
 

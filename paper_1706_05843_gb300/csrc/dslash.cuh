@@ -44,14 +44,22 @@ enum Kind {
     KIND_LOC_DTMINV = 8,   // out = D~ M^-1 y
     KIND_LOC_DT = 9,       // out = D~ y
     KIND_LOC_DTINV = 10,   // out = D~^-1 y
-    NKIND = 11
+    // even-odd on Eq. (non_hermit_sys) without the Cayley form (App. B):
+    // A = D_EOFA + beta g5 R5 Delta P, A_ee = A_oo dense in s, A_eo = -1/2 D_h
+    KIND_D_EO = 11,        // out = -1/2 A_ee^-1 D_h in
+    KIND_D_OE = 12,        // out = A_oo y + 1/2 D_h in
+    KIND_D_EO_DAG = 13,    // out = -1/2 A_ee^-T g5 D_h g5 in
+    KIND_D_OE_DAG = 14,    // out = A_oo^T y + 1/2 g5 D_h g5 in
+    NKIND = 15
 };
 
 template <int K> struct KindTraits {
-    static constexpr bool HOP = K <= KIND_FULL_DAG;
-    static constexpr bool DAG = K == KIND_EO_MINV_DAG || K == KIND_OE_SCHUR_DAG || K == KIND_FULL_DAG;
+    static constexpr bool DENSE = K >= KIND_D_EO && K <= KIND_D_OE_DAG;
+    static constexpr bool HOP = K <= KIND_FULL_DAG || DENSE;
+    static constexpr bool DAG = K == KIND_EO_MINV_DAG || K == KIND_OE_SCHUR_DAG || K == KIND_FULL_DAG ||
+                                K == KIND_D_EO_DAG || K == KIND_D_OE_DAG;
     static constexpr bool PRE = K == KIND_EO_MINV || K == KIND_RECON || K == KIND_FULL;
-    static constexpr bool HASY = !(K == KIND_EO_MINV || K == KIND_EO_MINV_DAG);
+    static constexpr bool HASY = !(K == KIND_EO_MINV || K == KIND_EO_MINV_DAG || K == KIND_D_EO || K == KIND_D_EO_DAG);
     // site-local kinds: the fifth-dimension part reaches only slices s-1, s+1
     // and the fixed slice of the rank-one shift, so each thread finishes its
     // own 5D site without the shared-memory column phase
@@ -69,6 +77,10 @@ struct HopArgs {
     const void* lk_in;                       // links of parity 1 - out_par
     Reduce rd;                               // rd.fin == FIN_NONE: no reduction
     const int* done;                         // early exit when *done != 0 (may be NULL)
+    // dense kinds: the Ls x Ls s-space matrix of each chirality in compute
+    // precision, [chirality][row][col] in mirrored coordinates
+    // (A_ee^-1 for the EO kinds, A_oo for the OE kinds)
+    const void* dense;
 };
 
 // ---------------------------------------------------------------------------
@@ -382,10 +394,39 @@ __device__ __forceinline__ void ld_half(const R* p, R* v) {
 // ycol: the local input; consecutive slices are ST reals apart.
 template <typename R, int LS, int KIND, int ST>
 __device__ __forceinline__ void column_program(R* hcol, const R* ycol, const SCoef<R>& cf, bool shv,
-                                               R hb) {
+                                               R hb, const R* mat) {
     typedef KindTraits<KIND> KT;
     C2<R> v[LS];
-    if constexpr (KIND == KIND_EO_MINV) {
+    if constexpr (KT::DENSE) {
+        // dense s-space matrix (row-major in mirrored coordinates) times the
+        // column, or its transpose for the adjoint kinds
+        constexpr bool TR = KT::DAG;
+        constexpr bool EO = (KIND == KIND_D_EO || KIND == KIND_D_EO_DAG);
+#pragma unroll
+        for (int k = 0; k < LS; ++k) v[k] = ld_pair((EO ? hcol : ycol) + k * ST);
+        C2<R> w[LS];
+#pragma unroll
+        for (int k = 0; k < LS; ++k) {
+            R re = (R)0, im = (R)0;
+#pragma unroll
+            for (int j = 0; j < LS; ++j) {
+                const R a = TR ? mat[j * LS + k] : mat[k * LS + j];
+                re = fma(a, v[j].re, re);
+                im = fma(a, v[j].im, im);
+            }
+            w[k] = {re, im};
+        }
+        if constexpr (EO) {
+#pragma unroll
+            for (int k = 0; k < LS; ++k) v[k] = {(R)(-0.5) * w[k].re, (R)(-0.5) * w[k].im};
+        } else {
+#pragma unroll
+            for (int k = 0; k < LS; ++k) {
+                const C2<R> h = ld_pair(hcol + k * ST);
+                v[k] = {w[k].re + (R)0.5 * h.re, w[k].im + (R)0.5 * h.im};
+            }
+        }
+    } else if constexpr (KIND == KIND_EO_MINV) {
 #pragma unroll
         for (int k = 0; k < LS; ++k) v[k] = ld_pair(hcol + k * ST);
         op_Minv<R, LS>(v, cf, shv);
@@ -642,7 +683,8 @@ __device__ __forceinline__ void hop_body(const HopArgs& a, const SCoef<typename 
     constexpr bool COLS = ShflTail<KIND, LS>::COLS;  // column phase and its tile buffers
     R* sh = reinterpret_cast<R*>(smem_raw);          // [NS][SS] hop result
     R* sy = sh + (COLS ? NS * SS : 0);                // [NS][SS] local input
-    R* sl = sy + ((KT::HASY && COLS) ? NS * SS : 0);  // [2][NL][LK] links, row 2 rebuilt
+    R* smat = sy + ((KT::HASY && COLS) ? NS * SS : 0);  // [2][LS][LS] dense kinds' s-matrices
+    R* sl = smat + (KT::DENSE ? 2 * LS * LS : 0);       // [2][NL][LK] links, row 2 rebuilt
     unsigned char* sraw = reinterpret_cast<unsigned char*>(sl + (KT::HOP ? 2 * NL * LK : 0));  // [2][NL][RAWB]
     unsigned* snb = reinterpret_cast<unsigned*>(sraw + (KT::HOP ? 2 * NL * RAWB : 0));        // [2][NL]
 
@@ -710,6 +752,10 @@ __device__ __forceinline__ void hop_body(const HopArgs& a, const SCoef<typename 
     };
 
     long blk = blockIdx.x;
+    if constexpr (KT::DENSE) {  // published by the barrier after the first links
+        const R* gm = reinterpret_cast<const R*>(a.dense);
+        for (int i = tid; i < 2 * LS * LS; i += NT) smat[i] = gm[i];
+    }
     if constexpr (KT::HOP) {
         if (blk < nblk) {
             stage_issue(blk, 0);
@@ -821,7 +867,8 @@ __device__ __forceinline__ void hop_body(const HopArgs& a, const SCoef<typename 
                 const int ci = col / 12;
                 const int cc = col - ci * 12;     // spin * 3 + colour
                 const bool shv = cf.has_shift && ((cc >= 6 ? 1 : 0) == cf.cs);
-                column_program<R, LS, KIND, ST>(sh + ci * SS + 2 * cc, sy + ci * SS + 2 * cc, cf, shv, hb);
+                column_program<R, LS, KIND, ST>(sh + ci * SS + 2 * cc, sy + ci * SS + 2 * cc, cf, shv, hb,
+                                                smat + (cc >= 6 ? LS * LS : 0));
             }
             __syncthreads();
         }
@@ -866,6 +913,7 @@ constexpr size_t hop_smem_bytes() {
     constexpr size_t bufs = ShflTail<K, LS>::COLS ? (1 + (KindTraits<K>::HASY ? 1 : 0)) : 0;
     constexpr size_t NL = (size_t)Tile<LS, VAR>::NS * 8;
     return bufs * (size_t)Tile<LS, VAR>::NS * SiteStride<R, LS>::V * sizeof(R) +
+           (KindTraits<K>::DENSE ? 2 * (size_t)LS * LS * sizeof(R) : 0) +
            (KindTraits<K>::HOP ? 2 * NL * (LinkStride<R>::V * sizeof(R) + LinkRaw<S>::PAD + sizeof(unsigned)) : 0);
 }
 

@@ -95,6 +95,10 @@ static cudaError_t launch_outer_ls(int kind, const HopArgs& a, const SCoef<typen
         case KIND_LOC_DTMINV: return launch_one<S, LS, KIND_LOC_DTMINV, 0>(a, c, st);
         case KIND_LOC_DT: return launch_one<S, LS, KIND_LOC_DT, 0>(a, c, st);
         case KIND_LOC_DTINV: return launch_one<S, LS, KIND_LOC_DTINV, 0>(a, c, st);
+        case KIND_D_EO: return launch_one<S, LS, KIND_D_EO, 0>(a, c, st);
+        case KIND_D_OE: return launch_one<S, LS, KIND_D_OE, 0>(a, c, st);
+        case KIND_D_EO_DAG: return launch_one<S, LS, KIND_D_EO_DAG, 0>(a, c, st);
+        case KIND_D_OE_DAG: return launch_one<S, LS, KIND_D_OE_DAG, 0>(a, c, st);
         default: return cudaErrorNotSupported;
     }
 }
@@ -113,7 +117,7 @@ static cudaError_t launch_inner_t(int kind, const HopArgs& a, const void* coef, 
     }
 }
 
-// kinds 4..10 (FP64 and FP32 storage)
+// kinds 4..14 (FP64 and FP32 storage)
 template <typename S>
 static cudaError_t launch_outer_t(int kind, const HopArgs& a, const void* coef, cudaStream_t st) {
     typedef typename Traits<S>::R R;

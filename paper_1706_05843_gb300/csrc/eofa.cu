@@ -69,10 +69,16 @@ struct eofa_ctx {
     // autotuned CTA tile variant of the four inner-solver hop kinds, per precision
     bool tuned[4] = {};
     int tile[4][4] = {};
-    // device-driven CG loops, one per inner precision
+    // device-driven CG loops, one per inner method and precision
     cudaStream_t cap = nullptr;
-    cudaGraphExec_t cg_exec[4] = {};
-    cudaGraphExec_t cg_first[4] = {};  // the first CG iteration, with timing events
+    cudaGraphExec_t cg_exec[2][4] = {};
+    cudaGraphExec_t cg_first[2][4] = {};  // the first CG iteration, with timing events
+    // inner operator of the current solve (opts.method): 0 Cayley form,
+    // 1 dense even-odd on the unpreconditioned system; the dense s-space
+    // matrices of method 1, [F64, F32][A_ee^-1, A_oo] -> [chirality][Ls][Ls]
+    int method = 0;
+    bool dense_ready = false;
+    void* dense[2][2] = {};
     // learned preconditioner: weights, activations of all Ls slices on the
     // full lattice, flexible-GCR vectors (FP32, odd parity), second
     // reduction buffers for complex inner products
@@ -275,6 +281,8 @@ eofa_status hop(eofa_ctx* c, int prec, int kind, int out_par, VecRef in, VecRef 
     a.rd = rd;
     a.tile_var = (kind <= KIND_OE_SCHUR_DAG && c->tuned[prec]) ? c->tile[prec][kind] : 0;
     a.done = done;
+    if (kind >= KIND_D_EO && kind <= KIND_D_OE_DAG && prec <= EOFA_F32)
+        a.dense = c->dense[prec][(kind == KIND_D_OE || kind == KIND_D_OE_DAG) ? 1 : 0];
     const void* coef = prec == EOFA_F64 ? (const void*)&c->c64 : (const void*)&c->c32;
     const bool tm = timed && c->timing;
     if (tm) {
@@ -457,6 +465,9 @@ eofa_status cg_iteration(eofa_ctx* c, int P, cudaStream_t st, bool timed, cudaEv
     const int xp = P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
     const int* done = &c->scal->done;
     const VecRef none{};
+    const bool dn = c->method == 1;  // the four Schur halves of the chosen inner operator
+    const int k0 = dn ? KIND_D_EO : KIND_EO_MINV, k1 = dn ? KIND_D_OE : KIND_OE_SCHUR;
+    const int k2 = dn ? KIND_D_EO_DAG : KIND_EO_MINV_DAG, k3 = dn ? KIND_D_OE_DAG : KIND_OE_SCHUR_DAG;
     eofa_status s;
     auto mark = [&](int i) -> eofa_status {
         // External: under stream capture this becomes an event record node
@@ -464,18 +475,17 @@ eofa_status cg_iteration(eofa_ctx* c, int P, cudaStream_t st, bool timed, cudaEv
         if (ev) CK(cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal), "cudaEventRecordWithFlags");
         return EOFA_OK;
     };
-    if ((s = mark(0)) || (s = hop(c, P, KIND_EO_MINV, 0, in.p, none, in.t, red(c, FIN_NONE), done, st, timed)) ||
+    if ((s = mark(0)) || (s = hop(c, P, k0, 0, in.p, none, in.t, red(c, FIN_NONE), done, st, timed)) ||
         (s = mark(1)))
         return s;
-    if ((s = mark(2)) || (s = hop(c, P, KIND_OE_SCHUR, 1, in.t, in.p, in.q, red(c, FIN_ALPHA), done, st, timed)) ||
+    if ((s = mark(2)) || (s = hop(c, P, k1, 1, in.t, in.p, in.q, red(c, FIN_ALPHA), done, st, timed)) ||
         (s = mark(3)))
         return s;
     CKL(blas_cg_r(P, in.q, in.r, c->n5, c->g.Ls, red(c, FIN_RR), done, st), "cg_r");
-    if ((s = mark(4)) || (s = hop(c, P, KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), done, st, timed)) ||
+    if ((s = mark(4)) || (s = hop(c, P, k2, 0, in.r, none, in.t, red(c, FIN_NONE), done, st, timed)) ||
         (s = mark(5)))
         return s;
-    if ((s = mark(6)) ||
-        (s = hop(c, P, KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_BETA), done, st, timed)) ||
+    if ((s = mark(6)) || (s = hop(c, P, k3, 1, in.t, in.r, in.z, red(c, FIN_BETA), done, st, timed)) ||
         (s = mark(7)))
         return s;
     CKL(blas_cg_px(P, xp, in.x, in.p, in.z, c->n5, c->g.Ls, red(c, FIN_STOP), st), "cg_px");
@@ -489,9 +499,12 @@ eofa_status cg_start(eofa_ctx* c, int P, const int* done, cudaStream_t st) {
     const int xp = P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
     const VecRef none{};
     eofa_status s;
+    const bool dn = c->method == 1;
     CKL(blas_zero(xp, in.x, c->n5, c->g.Ls, st), "blas_zero");
-    if ((s = hop(c, P, KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), done, st))) return s;
-    if ((s = hop(c, P, KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_ZZ), done, st))) return s;
+    if ((s = hop(c, P, dn ? KIND_D_EO_DAG : KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), done, st)))
+        return s;
+    if ((s = hop(c, P, dn ? KIND_D_OE_DAG : KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_ZZ), done, st)))
+        return s;
     CKL(blas_copy(P, in.p, P, in.z, c->n5, c->g.Ls, 1.0, -1, red(c, FIN_NONE), st), "blas_copy");
     return EOFA_OK;
 }
@@ -517,7 +530,7 @@ constexpr int kChunk = 16;  // iterations per graph body / per host check
 // kernel.  All pointers it bakes in belong to the context, so the graph is
 // replayed by every later solve.
 eofa_status build_cg_graph(eofa_ctx* c, int P) {
-    if (c->cg_exec[P]) return EOFA_OK;
+    if (c->cg_exec[c->method][P]) return EOFA_OK;
     if (!c->cap) CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "cudaStreamCreate");
     for (int i = 0; i < 8; ++i)
         if (!c->gev[P][i]) CK(cudaEventCreate(&c->gev[P][i]), "cudaEventCreate");
@@ -557,9 +570,9 @@ eofa_status build_cg_graph(eofa_ctx* c, int P) {
     c->launches = launches0;
     if (s == EOFA_OK && e2 != cudaSuccess) s = cuda_fail(c, e2, "cudaStreamEndCapture");
     if (s == EOFA_OK) {
-        e = cudaGraphInstantiate(&c->cg_exec[P], g, 0);
+        e = cudaGraphInstantiate(&c->cg_exec[c->method][P], g, 0);
         if (e != cudaSuccess) {
-            c->cg_exec[P] = nullptr;
+            c->cg_exec[c->method][P] = nullptr;
             s = cuda_fail(c, e, "cudaGraphInstantiate");
         }
     }
@@ -575,16 +588,16 @@ eofa_status build_cg_graph(eofa_ctx* c, int P) {
     c->launches = launches0;
     if (s == EOFA_OK && e2 != cudaSuccess) s = cuda_fail(c, e2, "cudaStreamEndCapture");
     if (s == EOFA_OK) {
-        e = cudaGraphInstantiate(&c->cg_first[P], g1, 0);
+        e = cudaGraphInstantiate(&c->cg_first[c->method][P], g1, 0);
         if (e != cudaSuccess) {
-            c->cg_first[P] = nullptr;
+            c->cg_first[c->method][P] = nullptr;
             s = cuda_fail(c, e, "cudaGraphInstantiate");
         }
     }
     if (g1) cudaGraphDestroy(g1);
-    if (s != EOFA_OK && c->cg_exec[P]) {
-        cudaGraphExecDestroy(c->cg_exec[P]);
-        c->cg_exec[P] = nullptr;
+    if (s != EOFA_OK && c->cg_exec[c->method][P]) {
+        cudaGraphExecDestroy(c->cg_exec[c->method][P]);
+        c->cg_exec[c->method][P] = nullptr;
     }
     return s;
 }
@@ -607,8 +620,8 @@ eofa_status run_cgnr(eofa_ctx* c, int P, double tol, int maxit, int* iters, doub
     *iters = 0;
     if (!c->timing) {
         if ((s = build_cg_graph(c, P))) return s;
-        CK(cudaGraphLaunch(c->cg_first[P], st), "cudaGraphLaunch");
-        CK(cudaGraphLaunch(c->cg_exec[P], st), "cudaGraphLaunch");
+        CK(cudaGraphLaunch(c->cg_first[c->method][P], st), "cudaGraphLaunch");
+        CK(cudaGraphLaunch(c->cg_exec[c->method][P], st), "cudaGraphLaunch");
         if ((s = read_scal(c, st))) return s;
         const DevScal& h = *c->h_scal;
         *iters = h.iters;
@@ -673,6 +686,112 @@ eofa_status enqueue_read(eofa_ctx* c, cudaStream_t st) {
 // Phase 1: options, b = g5 R5 phi (H form) or b (K form) with |b|^2 into
 // store[1] + store[2], the odd part of the initial guess, the even-odd
 // source b~o = b_o + 1/2 D_h D~ M^-1 b_e.  Ends with a read-back enqueued.
+// Dense Ls x Ls inverse by Gauss-Jordan elimination with partial pivoting
+// (row-major, n <= 32); false when singular.
+bool dense_inverse(int n, const double* a, double* inv) {
+    double m[32][64];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < 2 * n; ++j) m[i][j] = j < n ? a[i * n + j] : (j - n == i ? 1.0 : 0.0);
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int i = col + 1; i < n; ++i)
+            if (std::fabs(m[i][col]) > std::fabs(m[piv][col])) piv = i;
+        if (!(std::fabs(m[piv][col]) > 1e-300)) return false;
+        if (piv != col)
+            for (int j = 0; j < 2 * n; ++j) std::swap(m[piv][j], m[col][j]);
+        const double d = 1.0 / m[col][col];
+        for (int j = 0; j < 2 * n; ++j) m[col][j] *= d;
+        for (int i = 0; i < n; ++i) {
+            if (i == col) continue;
+            const double f = m[i][col];
+            if (f != 0.0)
+                for (int j = 0; j < 2 * n; ++j) m[i][j] -= f * m[col][j];
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) inv[i * n + j] = m[i][n + j];
+    return true;
+}
+
+// The s-space blocks of the unpreconditioned even-odd scheme (App. B):
+// the site-diagonal block of Eq. (non_hermit_sys) on chirality chi is
+// A_chi = K_chi D~^-1, with K_chi = alpha + gamma L+ (+ the rank-one shift on
+// the shift chirality) the site-diagonal block of the Cayley form and
+// D~ = b5 + c5 L+ (mirrored coordinates, L+ with -m1 across the wall): the
+// Cayley identity K = A D~ restricted to one site.  A_ee^-1 = D~ K_chi^-1
+// and A_oo = K_chi D~^-1 are formed densely at set-up (FP64), as the dense
+// scheme does, and the four dense kinds are launched once here, before any
+// graph capture needs them.
+eofa_status ensure_dense(eofa_ctx* c, cudaStream_t st) {
+    if (c->dense_ready) return EOFA_OK;
+    const int n = c->g.Ls;
+    const SCoef<double>& k = c->c64;
+    std::vector<double> dt(n * n, 0.0), kc(n * n), dti(n * n), kci(n * n);
+    std::vector<double> host[2];  // [A_ee^-1, A_oo] as [chi][n][n]
+    host[0].assign(2 * n * n, 0.0);
+    host[1].assign(2 * n * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        dt[i * n + i] = k.b5;
+        if (i > 0) dt[i * n + i - 1] = k.c5;
+    }
+    dt[0 * n + n - 1] = -k.m * k.c5;
+    if (!dense_inverse(n, dt.data(), dti.data())) return fail(c, EOFA_ERR_SINGULAR, "D~ is singular");
+    for (int chi = 0; chi < 2; ++chi) {
+        std::fill(kc.begin(), kc.end(), 0.0);
+        for (int i = 0; i < n; ++i) {
+            kc[i * n + i] = k.alpha;
+            if (i > 0) kc[i * n + i - 1] = k.gamma;
+        }
+        kc[0 * n + n - 1] = -k.m * k.gamma;
+        if (k.has_shift && chi == k.cs)
+            for (int i = 0; i < n; ++i) kc[i * n + n - 1] += k.sbk * k.um[i];
+        if (!dense_inverse(n, kc.data(), kci.data()))
+            return fail(c, EOFA_ERR_SINGULAR, "site-diagonal block is singular");
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                double ainv = 0.0, a = 0.0;
+                for (int l = 0; l < n; ++l) {
+                    ainv += dt[i * n + l] * kci[l * n + j];
+                    a += kc[i * n + l] * dti[l * n + j];
+                }
+                host[0][(chi * n + i) * n + j] = ainv;
+                host[1][(chi * n + i) * n + j] = a;
+            }
+    }
+    for (int w = 0; w < 2; ++w) {
+        std::vector<float> f(host[w].begin(), host[w].end());
+        eofa_status s;
+        if ((s = dalloc(c, &c->dense[EOFA_F64][w], sizeof(double) * 2 * n * n)) ||
+            (s = dalloc(c, &c->dense[EOFA_F32][w], sizeof(float) * 2 * n * n)))
+            return s;
+        CK(cudaMemcpy(c->dense[EOFA_F64][w], host[w].data(), sizeof(double) * 2 * n * n, cudaMemcpyHostToDevice),
+           "cudaMemcpy");
+        CK(cudaMemcpy(c->dense[EOFA_F32][w], f.data(), sizeof(float) * 2 * n * n, cudaMemcpyHostToDevice),
+           "cudaMemcpy");
+    }
+    const VecRef none{};
+    eofa_status s0;
+    if ((s0 = ensure_inner(c, EOFA_F32))) return s0;
+    for (int P : {EOFA_F64, EOFA_F32}) {
+        eofa_status s;
+        // operands: the context's FP64 work vectors (before the solution is
+        // imported), or the FP32 inner vectors
+        const Inner& in = c->inner[EOFA_F32];
+        const VecRef oa = P == EOFA_F64 ? c->x[1] : in.p, ev = P == EOFA_F64 ? c->t[0] : in.t,
+                     ob = P == EOFA_F64 ? c->qo : in.q;
+        const size_t bytes = (size_t)c->n5 * 24 * kWidth[P];
+        for (VecRef v : {oa, ev, ob}) CK(cudaMemsetAsync(v.d, 0, bytes, st), "memset");
+        if ((s = hop(c, P, KIND_D_EO, 0, oa, none, ev, red(c, FIN_NONE), nullptr, st)) ||
+            (s = hop(c, P, KIND_D_OE, 1, ev, oa, ob, red(c, FIN_NONE), nullptr, st)) ||
+            (s = hop(c, P, KIND_D_EO_DAG, 0, oa, none, ev, red(c, FIN_NONE), nullptr, st)) ||
+            (s = hop(c, P, KIND_D_OE_DAG, 1, ev, oa, ob, red(c, FIN_NONE), nullptr, st)))
+            return s;
+    }
+    CK(cudaStreamSynchronize(st), "sync");
+    c->dense_ready = true;
+    return EOFA_OK;
+}
+
 eofa_status solve_begin(eofa_ctx* c, const double* rhs, const double* sol, const eofa_solve_opts& o,
                         SolveState& ss, cudaStream_t st) {
     ss.t0 = Clock::now();
@@ -684,6 +803,10 @@ eofa_status solve_begin(eofa_ctx* c, const double* rhs, const double* sol, const
         if (!c->net_ready) return fail(c, EOFA_ERR_UNSUPPORTED, "no preconditioner: call eofa_set_preconditioner");
         if (ss.P != EOFA_F32) return fail(c, EOFA_ERR_UNSUPPORTED, "the learned preconditioner runs with inner FP32");
     }
+    if (o.method != 0 && o.method != 1) return fail(c, EOFA_ERR_ARG, "opts.method must be 0 or 1");
+    if (o.method == 1 && (ss.P > EOFA_F32 || o.precond != 0))
+        return fail(c, EOFA_ERR_UNSUPPORTED, "the dense scheme runs with FP64 or FP32 inner and no preconditioner");
+    c->method = o.method;
     ss.maxit = o.max_iter > 0 ? o.max_iter : 100000;
     ss.maxouter = o.max_outer > 0 ? o.max_outer : 100;
     ss.H = o.rhs_form == 0 ? 1 : 0;
@@ -691,6 +814,7 @@ eofa_status solve_begin(eofa_ctx* c, const double* rhs, const double* sol, const
     eofa_status s;
     if ((s = ensure_inner(c, ss.P))) return s;
     if ((s = autotune(c, ss.P, st)) || (s = autotune(c, EOFA_F64, st))) return s;
+    if (c->method == 1 && (s = ensure_dense(c, st))) return s;
     c->timing = o.kernel_timing != 0;
     c->launches = 0;
     c->gcr_steps = c->gcr_fallbacks = 0;
@@ -848,7 +972,16 @@ eofa_status solve_impl(eofa_ctx* c, const double* rhs, double* sol, const eofa_s
             ss.result = is;
             break;
         }
-        CKL(blas_acc(c->x[1], ss.xp, c->inner[ss.P].x, c->n5, Ls, c->scal, 0, st), "acc");
+        VecRef e = c->inner[ss.P].x;
+        if (c->method == 1) {
+            // the dense scheme's correction is in psi; the outer iterate is
+            // psi' = D~^-1 psi
+            if ((s = hop(c, ss.xp, KIND_LOC_DTINV, 1, VecRef{}, e, c->inner[ss.P].z, red(c, FIN_NONE), nullptr,
+                         st)))
+                return s;
+            e = c->inner[ss.P].z;
+        }
+        CKL(blas_acc(c->x[1], ss.xp, e, c->n5, Ls, c->scal, 0, st), "acc");
         ss.x_zero = false;
     }
     return solve_end(c, sol, o, ss, stats, st);
@@ -1163,9 +1296,10 @@ eofa_status eofa_solve_batched(eofa_ctx* const* ctx, int n, const void* const* r
         for (int j = 0; j < i; ++j)
             if (ctx[j] == ctx[i]) return EOFA_ERR_ARG;  // one context per system
     }
-    // kernel timing instruments the host-driven loop, and the learned
-    // preconditioner runs flexible GCR: both solve one by one
-    if (opts->kernel_timing || opts->precond || opts->inner < 0 || opts->inner > 3) {
+    // kernel timing instruments the host-driven loop, the learned
+    // preconditioner runs flexible GCR, and the dense comparison scheme has
+    // no batched loop: these solve one by one
+    if (opts->kernel_timing || opts->precond || opts->method || opts->inner < 0 || opts->inner > 3) {
         eofa_status first = EOFA_OK;
         for (int i = 0; i < n; ++i) {
             eofa_status s = eofa_solve(ctx[i], rhs[i], sol[i], opts, stats ? stats + i : nullptr, stream);
@@ -1193,8 +1327,10 @@ void eofa_destroy(eofa_ctx* ctx) {
         for (cudaEvent_t e : row)
             if (e) cudaEventDestroy(e);
     for (int i = 0; i < 4; ++i) {
-        if (ctx->cg_exec[i]) cudaGraphExecDestroy(ctx->cg_exec[i]);
-        if (ctx->cg_first[i]) cudaGraphExecDestroy(ctx->cg_first[i]);
+        for (int m = 0; m < 2; ++m) {
+            if (ctx->cg_exec[m][i]) cudaGraphExecDestroy(ctx->cg_exec[m][i]);
+            if (ctx->cg_first[m][i]) cudaGraphExecDestroy(ctx->cg_first[m][i]);
+        }
     }
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);

@@ -117,6 +117,34 @@ def test_solve_with_guess_and_zero_rhs(env):
     s.close()
 
 
+@pytest.mark.parametrize("case", [CASES[0], CASES[2], CASES[5], CASES[6]], ids=[IDS[0], IDS[2], IDS[5], IDS[6]])
+@pytest.mark.parametrize("inner", ["f64", "f32"])
+def test_solve_dense_scheme(env, case, inner):
+    """The dense even-odd scheme (no Cayley form, dense Ls x Ls site block,
+    App. B) solves the same EOFA system: the oracle's operator judges the
+    answer, which agrees with the Cayley-form solve."""
+    torch, s, o = setup(env, case)
+    phi = I.gaussian_fermion(case[0], case[1], 1001)
+    x = torch.from_numpy(phi).cuda()
+    psi_d, st_d = s.solve(x, tol=1e-10, inner=inner, method=1)
+    psi_c, st_c = s.solve(x, tol=1e-10, inner=inner)
+    assert st_d.status == 0 and st_d.inner_iters > 0
+    assert rel(o.hsys(psi_d.cpu().numpy()), phi) <= 1e-10, st_d.as_dict()
+    assert rel(psi_d.cpu().numpy(), psi_c.cpu().numpy()) < 1e-8
+    print(f"{case[0]} Ls={case[1]} {inner}: dense {st_d.inner_iters} iterations, Cayley {st_c.inner_iters}")
+    s.close()
+
+
+def test_dense_scheme_rejects_16bit(env):
+    torch, s, o = setup(env, CASES[0])
+    from paper_1706_05843_gb300 import binding as B
+    x = torch.from_numpy(I.gaussian_fermion(CASES[0][0], CASES[0][1], 1001)).cuda()
+    with pytest.raises(B.EofaError) as ei:
+        s.solve(x, tol=1e-10, inner="f16", method=1)
+    assert ei.value.status == 2
+    s.close()
+
+
 def test_hop_timing_stats(env):
     """Both timing modes report hop launches, time and algorithmic bytes: the
     graph path a sample of four launches per inner solve, kernel timing every
