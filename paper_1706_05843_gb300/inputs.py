@@ -125,6 +125,15 @@ def gaussian_fermion(dims, Ls: int, seed: int) -> np.ndarray:
     return d[..., 0] + 1j * d[..., 1]
 
 
+def heatbath_noise(dims, seed: int) -> np.ndarray:
+    """The heatbath's 4D Gaussian eta: real and imaginary parts N(0, 1/2), so
+    that P(eta) ~ exp(-eta^dag eta) (Sec. III.B).  Shape (T, Z, Y, X, 4, 3)."""
+    X, Y, Z, T = (int(d) for d in dims)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d = rng.standard_normal((T, Z, Y, X, 4, 3, 2)) * np.sqrt(0.5)
+    return d[..., 0] + 1j * d[..., 1]
+
+
 def gaussian_fermion_batch(dims, Ls: int, seeds) -> np.ndarray:
     """Stack of ``gaussian_fermion`` fields, one per seed."""
     return np.stack([gaussian_fermion(dims, Ls, s) for s in seeds])

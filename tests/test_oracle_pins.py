@@ -296,15 +296,11 @@ def test_det_ratio_dwf_vs_eofa(dense24):
     assert abs(sW1 / sW2 - sE1 / sE2) < 1e-9
 
 
-def test_det_ratio_equals_m_eofa(oracle_mod, dense24):
-    """Eqs. (EOFA_factorization), (eofa_action), (eofa_pi):
-    det D_EOFA(m1) / det D_EOFA(m2) = 1 / det M_EOFA, and M_EOFA is
-    Hermitian positive definite (its spectrum is not asserted to start at 1:
-    the paper's '1.0' is rounded and random fields give ~0.99)."""
-    d = dense24
+def dense_meofa(O, d):
+    """Dense M_EOFA(m1, m2) of Eq. (eofa_action) from dense H(m1), H(m2)."""
     o, V, Ls = d["o"], d["V"], d["Ls"]
     m1, m2 = d["m1"], d["m2"]
-    g5 = oracle_mod.gamma(4)
+    g5 = O.gamma(4)
     k = o.kcoef(m1, m2)
     Omp = omega_matrix(o.omega(1), V, Ls)
     Omm = omega_matrix(o.omega(-1), V, Ls)
@@ -312,8 +308,17 @@ def test_det_ratio_equals_m_eofa(oracle_mod, dense24):
     Dp = site_smatrix(o.delta(m1, m2, 1), np.zeros((Ls, Ls)), V, Ls, g5)
     Hm = np.linalg.inv(d["H1"])
     Hp = np.linalg.inv(d["H2"] - Dp)
-    M = (np.eye(12 * V) - k * Pm4 @ Omm.T @ Hm @ Omm @ Pm4
-         + k * Pp4 @ Omp.T @ Hp @ Omp @ Pp4)
+    return (np.eye(12 * V) - k * Pm4 @ Omm.T @ Hm @ Omm @ Pm4
+            + k * Pp4 @ Omp.T @ Hp @ Omp @ Pp4)
+
+
+def test_det_ratio_equals_m_eofa(oracle_mod, dense24):
+    """Eqs. (EOFA_factorization), (eofa_action), (eofa_pi):
+    det D_EOFA(m1) / det D_EOFA(m2) = 1 / det M_EOFA, and M_EOFA is
+    Hermitian positive definite (its spectrum is not asserted to start at 1:
+    the paper's '1.0' is rounded and random fields give ~0.99)."""
+    d = dense24
+    M = dense_meofa(oracle_mod, d)
     assert np.abs(M - M.conj().T).max() < 1e-12
     ev = np.linalg.eigvalsh(0.5 * (M + M.conj().T))
     assert ev.min() > 0.5
@@ -322,6 +327,67 @@ def test_det_ratio_equals_m_eofa(oracle_mod, dense24):
     sM, lM = np.linalg.slogdet(M)
     assert abs((lE1 - lE2) + lM) < 1e-9
     assert abs(sM - 1) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# M_EOFA application and heatbath (Eqs. eofa_action, eofa_heatbath)
+# --------------------------------------------------------------------------
+def test_meofa_apply_matches_dense(oracle_mod, dense24):
+    """The oracle's M_EOFA phi (two H-form solves and the Omega projections)
+    equals the dense M_EOFA built from inverted dense H matrices."""
+    from oracle import action as A
+    d = dense24
+    o = d["o"]
+    M = dense_meofa(oracle_mod, d)
+    eta = I.heatbath_noise(o.a.dims, 5)
+    out, st = A.meofa(o.a, o.U, d["m1"], d["m2"], eta)
+    assert all(s.converged for s in st)
+    assert rel(out.reshape(-1), M @ eta.reshape(-1)) < 1e-10
+
+
+def test_heatbath_woodbury_identity(oracle_mod, dense24):
+    """Eq. (eofa_heatbath) is the Woodbury rewrite of
+    alpha_0 + sum_l alpha_l (M_EOFA + beta_l)^-1: the two agree for any
+    coefficients, not only those of a good approximation to x^(-1/2)."""
+    from oracle import action as A
+    d = dense24
+    o = d["o"]
+    M = dense_meofa(oracle_mod, d)
+    eta = I.heatbath_noise(o.a.dims, 6)
+    a0, al, bl = 0.3, [0.7, 0.2, 1.3], [0.05, 0.9, 4.0]
+    phi, st = A.heatbath(o.a, o.U, d["m1"], d["m2"], a0, al, bl, eta)
+    assert len(st) == 6 and all(s.converged for s in st)
+    n = M.shape[0]
+    ref = a0 * eta.reshape(-1)
+    for a, b in zip(al, bl):
+        ref = ref + a * np.linalg.solve(M + b * np.eye(n), eta.reshape(-1))
+    assert rel(phi.reshape(-1), ref) < 1e-10
+
+
+def test_heatbath_error_falls_with_poles(oracle_mod, dense24):
+    """epsilon of Eq. (heatbath_rel_err) falls with the number of poles, and
+    with enough poles phi is M_EOFA^(-1/2) eta to double precision (Sec. III.B,
+    Fig. 2 left: a modest pole count reaches double precision)."""
+    from oracle import action as A
+    from paper_1706_05843_gb300 import rational
+    d = dense24
+    o = d["o"]
+    M = dense_meofa(oracle_mod, d)
+    Mh = 0.5 * (M + M.conj().T)
+    w, Q = np.linalg.eigh(Mh)
+    eta = I.heatbath_noise(o.a.dims, 7)
+    e = eta.reshape(-1)
+    exact = Q @ ((Q.conj().T @ e) / np.sqrt(w))
+    eps = []
+    for n in (2, 4, 10):
+        r = rational.inv_sqrt(n, 0.95 * w[0], 1.05 * w[-1])
+        phi, _ = A.heatbath(o.a, o.U, d["m1"], d["m2"], r.alpha0, r.alpha, r.beta, eta)
+        mphi, _ = A.meofa(o.a, o.U, d["m1"], d["m2"], phi)
+        eps.append(A.heatbath_error(eta, phi, mphi))
+        # |phi - M^-1/2 eta| <= err |M^-1/2 eta| up to the solver tolerance
+        assert rel(phi.reshape(-1), exact) <= 1.01 * r.err + 1e-11
+    assert eps[0] > eps[1] > eps[2]
+    assert eps[2] < 1e-12
 
 
 # --------------------------------------------------------------------------
