@@ -158,6 +158,63 @@ eofa_status eofa_solve(eofa_ctx *ctx, const void *rhs, void *sol,
                        const eofa_solve_opts *opts, eofa_solve_stats *stats,
                        void *stream);
 
+/* ---------------------------------------------------------------------------
+ * EOFA action and heatbath (Sec. III.A Eq. eofa_action, Sec. III.B
+ * Eq. eofa_heatbath, App. A).  These reuse the context's lattice and gauge
+ * field with other masses, shifts and chiralities: eofa_set_system switches
+ * the context's own system; the two action calls switch it per solve and
+ * restore the caller's system before they return (also on failure).
+ *
+ * 4D fields (phi, out, eta): device complex128 [t][z][y][x][spin][colour],
+ * 24 * X*Y*Z*T doubles.  Omega_pm and k are the App. A closed forms for the
+ * context's Moebius b, c and Ls.  Every solve is an H-form eofa_solve with
+ * the caller's opts (tol, inner precision, method, max_iter, timeout; rhs_form
+ * and use_guess are set by the call).  A solve that does not converge
+ * leaves its best iterate in the result and its status in stats; the call
+ * then returns EOFA_ERR_NOT_CONVERGED after finishing every solve.  Any
+ * other failing status stops the call.  The calls allocate canonical 5D work
+ * fields (three plus two per forecast vector, 24 * Ls * X*Y*Z*T doubles
+ * each) in the context on first use and keep them until eofa_destroy.
+ * ------------------------------------------------------------------------- */
+
+/* Make the context solve (H(m1) + beta Delta_pm(m2, m3) P_pm) psi = phi:
+ * the fifth-dimension coefficients are rebuilt on the host; the captured
+ * solver graphs are rebuilt at the next solve.  EOFA_ERR_ARG for |pm| != 1
+ * or non-finite values; EOFA_ERR_SINGULAR as for eofa_create (the context
+ * then keeps its previous system). */
+eofa_status eofa_set_system(eofa_ctx *ctx, double m1, double m2, double m3, double beta, int pm);
+
+/* out = M_EOFA(m1, m2) phi, Eq. (eofa_action):
+ *   phi - k P_- Omega_-^dag H(m1)^-1 Omega_- P_- phi
+ *       + k P_+ Omega_+^dag [H(m2) - Delta_+(m1, m2) P_+]^-1 Omega_+ P_+ phi,
+ * k = k(m1, m2).  Two H-form solves; stats: NULL or 2 entries (the minus,
+ * then the plus term).  phi != out.  Returns after the work has finished. */
+eofa_status eofa_apply_meofa(eofa_ctx *ctx, double m1, double m2, const void *phi, void *out,
+                             const eofa_solve_opts *opts, eofa_solve_stats *stats, void *stream);
+
+/* phi = M_EOFA(m1, m2)^(-1/2) eta through the rational approximation
+ * x^(-1/2) ~ alpha[0] + sum_{l<np} alpha[l+1] / (x + beta[l]) in the form of
+ * Eq. (eofa_heatbath): with gamma_l = 1 / (1 + beta_l),
+ *   phi = alpha_0 eta + sum_l alpha_l gamma_l { eta
+ *         + k gamma_l P_- Omega_-^dag [H(m1) - gamma_l Delta_-(m1, m2) P_-]^-1 Omega_- P_- eta
+ *         - k gamma_l P_+ Omega_+^dag [H(m2) - beta_l gamma_l Delta_+(m1, m2) P_+]^-1 Omega_+ P_+ eta }.
+ * 2 np H-form solves, per pole the minus then the plus term.
+ * alpha: np + 1 host doubles; beta: np host doubles, each > -1.
+ * pole_tol: NULL, or 2 np host tolerances replacing opts->tol per solve
+ *   (entry 2l the minus, 2l+1 the plus solve of pole l; <= 0 keeps
+ *   opts->tol): the per-pole stopping conditions of Sec. V.B.
+ * forecast_n: 0, or up to 8: each solve starts from the chronological
+ *   guess of Sec. V.B, sum_k c_k psi_k over the last forecast_n solutions
+ *   psi_k of the same term, with sum_k c_k psi_l^dag A psi_k = psi_l^dag b for
+ *   the current system A and source b (Gauss-Jordan on the host; no guess
+ *   when that small system is singular).
+ * stats: NULL or 2 np entries in solve order.  eta != phi.  Returns after
+ * the work has finished. */
+eofa_status eofa_heatbath(eofa_ctx *ctx, double m1, double m2, int np, const double *alpha,
+                          const double *beta, const double *pole_tol, int forecast_n,
+                          const void *eta, void *phi, const eofa_solve_opts *opts,
+                          eofa_solve_stats *stats, void *stream);
+
 /* out[i] = K in[i] (dag = 0) or K^dag in[i] (dag = 1) for n contexts,
  * which may have different lattices. */
 eofa_status eofa_apply_batched(eofa_ctx *const *ctx, int n, const void *const *in,

@@ -73,6 +73,7 @@ class eofa_train_stats(C.Structure):
 # name -> (argtypes, restype); must match include/eofa.h
 _vp = C.c_void_p
 _fp = C.POINTER(C.c_float)
+_dp = C.POINTER(C.c_double)
 SIGNATURES = {
     "eofa_create": ([C.POINTER(eofa_params), _vp, _vp, C.POINTER(_vp)], C.c_int),
     "eofa_apply": ([_vp, _vp, _vp, _vp], C.c_int),
@@ -94,6 +95,11 @@ SIGNATURES = {
     "eofa_hop_bytes": ([_vp, C.c_int, C.c_int], C.c_double),
     "eofa_tile_sites": ([_vp, C.c_int, C.c_int], C.c_int),
     "eofa_tile_variant": ([_vp, C.c_int, C.c_int], C.c_int),
+    "eofa_set_system": ([_vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int], C.c_int),
+    "eofa_apply_meofa": ([_vp, C.c_double, C.c_double, _vp, _vp, C.POINTER(eofa_solve_opts),
+                          C.POINTER(eofa_solve_stats), _vp], C.c_int),
+    "eofa_heatbath": ([_vp, C.c_double, C.c_double, C.c_int, _dp, _dp, _dp, C.c_int, _vp, _vp,
+                       C.POINTER(eofa_solve_opts), C.POINTER(eofa_solve_stats), _vp], C.c_int),
 }
 
 _lib = None
@@ -183,6 +189,42 @@ def eofa_solve(ctx, rhs, sol, opts, stream=None, check=True):
     if check:
         _check(ctx, s)
     return st
+
+
+def eofa_set_system(ctx, m1, m2, m3, beta, pm):
+    _check(ctx, lib().eofa_set_system(ctx, float(m1), float(m2), float(m3), float(beta), int(pm)))
+
+
+def eofa_apply_meofa(ctx, m1, m2, phi, out, opts, stream=None, check=True):
+    st = (eofa_solve_stats * 2)()
+    s = lib().eofa_apply_meofa(ctx, float(m1), float(m2), _dptr(phi), _dptr(out), C.byref(opts), st,
+                               _stream(stream))
+    if check:
+        _check(ctx, s)
+    return list(st)
+
+
+def _doubles(v):
+    a = np.ascontiguousarray(v, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def eofa_heatbath(ctx, m1, m2, alpha0, alpha, beta, eta, phi, opts, pole_tol=None, forecast=0, stream=None,
+                  check=True):
+    np_ = len(beta)
+    if len(alpha) != np_:
+        raise ValueError("alpha and beta need one entry per pole")
+    a, ap = _doubles([alpha0, *alpha])
+    b, bp = _doubles(beta if np_ else [0.0])
+    t, tp = (None, None) if pole_tol is None else _doubles(pole_tol)
+    if t is not None and len(t) != 2 * np_:
+        raise ValueError("pole_tol needs two entries per pole")
+    st = (eofa_solve_stats * max(1, 2 * np_))()
+    s = lib().eofa_heatbath(ctx, float(m1), float(m2), np_, ap, bp, tp, int(forecast), _dptr(eta), _dptr(phi),
+                            C.byref(opts), st, _stream(stream))
+    if check:
+        _check(ctx, s)
+    return list(st)[:2 * np_]
 
 
 def eofa_apply_batched(ctxs, ins, outs, dag=False, stream=None):
@@ -315,6 +357,31 @@ class Solver:
 
     def hop_bytes(self, prec, with_local):
         return eofa_hop_bytes(self.ctx, prec, with_local)
+
+    @property
+    def shape4(self):
+        X, Y, Z, T = self.dims
+        return (T, Z, Y, X, 4, 3)
+
+    def set_system(self, m1, m2, m3, beta, pm):
+        eofa_set_system(self.ctx, m1, m2, m3, beta, pm)
+
+    def apply_meofa(self, phi, m1, m2, stream=None, check=True, **opts):
+        """M_EOFA(m1, m2) phi for a 4D field; returns (out, [minus, plus] stats)."""
+        import torch
+        out = torch.empty(self.shape4, dtype=torch.complex128, device="cuda")
+        st = eofa_apply_meofa(self.ctx, m1, m2, phi, out, make_opts(**opts), stream, check)
+        return out, st
+
+    def heatbath(self, eta, m1, m2, approx, pole_tol=None, forecast=0, stream=None, check=True, **opts):
+        """M_EOFA(m1, m2)^(-1/2) eta with the rational approximation ``approx``
+        (alpha0, alpha, beta attributes, e.g. rational.InvSqrt); returns
+        (phi, stats of the 2 N_p solves)."""
+        import torch
+        phi = torch.empty(self.shape4, dtype=torch.complex128, device="cuda")
+        st = eofa_heatbath(self.ctx, m1, m2, approx.alpha0, approx.alpha, approx.beta, eta, phi,
+                           make_opts(**opts), pole_tol, forecast, stream, check)
+        return phi, st
 
     def close(self):
         eofa_destroy(self.ctx)

@@ -57,4 +57,26 @@ cudaError_t slice_norm(VecRef f, long vh, int Ls, int sl, Reduce rd, cudaStream_
 cudaError_t loss_grad(const float* out, const __nv_bfloat16* e, const float* w, float* dout, const Geom& g, int B,
                       Reduce rd, cudaStream_t st);
 
+// EOFA action and heatbath (action.cu); canonical complex128 fields
+constexpr int kMultiMax = 8;       // vectors of one multi-dot or combination
+constexpr int kMultiBlocks = 1024; // fixed first-stage grid of the multi-dot
+struct OmegaW {
+    double w[LSMAX];  // Omega_pm as weights over s (App. A)
+};
+struct VecSet {
+    const double2* v[kMultiMax];
+    double2 c[kMultiMax];  // coefficients of combine
+    int n;
+};
+// out5 = Omega P_chi xi4 (om.w[s] times the chi half of xi4)
+cudaError_t omega_in(double* out5, const double* xi4, const OmegaW& om, int chi, long V, int Ls, cudaStream_t st);
+// out4 = a base4 + coef P_chi Omega^dag psi5 (psi5 NULL: out4 = a base4)
+cudaError_t omega_out(double* out4, const double* base4, double a, const double* psi5, const OmegaW& om, int chi,
+                      double coef, long V, int Ls, cudaStream_t st);
+// out[j] = <v_j, w> for j < set.n (n complex elements; partial holds
+// kMultiBlocks * kMultiMax complex values)
+cudaError_t multidot(const VecSet& set, const double* w, long n, double* partial, double* out, cudaStream_t st);
+// out = sum_j set.c[j] set.v[j]
+cudaError_t combine(double* out, const VecSet& set, long n, cudaStream_t st);
+
 }  // namespace eofa

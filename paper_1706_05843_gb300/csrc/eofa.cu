@@ -89,6 +89,10 @@ struct eofa_ctx {
     VecRef gx{}, gr{}, gz[4]{}, gw[4]{};
     double* partials2 = nullptr;
     unsigned* counter2 = nullptr;
+    // EOFA action and heatbath: canonical complex128 5D work fields,
+    // allocated on first use; multi-dot partial sums and results
+    std::vector<double*> act5;
+    double* mdot = nullptr;
 };
 
 namespace {
@@ -761,8 +765,10 @@ eofa_status ensure_dense(eofa_ctx* c, cudaStream_t st) {
     for (int w = 0; w < 2; ++w) {
         std::vector<float> f(host[w].begin(), host[w].end());
         eofa_status s;
-        if ((s = dalloc(c, &c->dense[EOFA_F64][w], sizeof(double) * 2 * n * n)) ||
-            (s = dalloc(c, &c->dense[EOFA_F32][w], sizeof(float) * 2 * n * n)))
+        // kept across eofa_set_system, which only changes their contents
+        if (!c->dense[EOFA_F64][w] &&
+            ((s = dalloc(c, &c->dense[EOFA_F64][w], sizeof(double) * 2 * n * n)) ||
+             (s = dalloc(c, &c->dense[EOFA_F32][w], sizeof(float) * 2 * n * n))))
             return s;
         CK(cudaMemcpy(c->dense[EOFA_F64][w], host[w].data(), sizeof(double) * 2 * n * n, cudaMemcpyHostToDevice),
            "cudaMemcpy");
@@ -1184,6 +1190,276 @@ eofa_status apply_impl(eofa_ctx* c, const void* in, void* out, int which, cudaSt
     return EOFA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// EOFA action M_EOFA and heatbath (Eqs. eofa_action, eofa_heatbath)
+// ---------------------------------------------------------------------------
+// App. A, Moebius kernel, with c + d = b5, c - d = c5:
+// Omega_+(s) = (-1)^(s+1) c5^(Ls-s-1) / b5^(Ls-s),  Omega_-(s) = (-1)^s c5^s / b5^(s+1)
+OmegaW omega_of(const eofa_params& p, int pm) {
+    OmegaW o{};
+    const int Ls = p.Ls;
+    for (int s = 0; s < Ls; ++s) {
+        if (pm > 0)
+            o.w[s] = ((s + 1) & 1 ? -1.0 : 1.0) * std::pow(p.c, Ls - s - 1) / std::pow(p.b, Ls - s);
+        else
+            o.w[s] = (s & 1 ? -1.0 : 1.0) * std::pow(p.c, s) / std::pow(p.b, s + 1);
+    }
+    return o;
+}
+
+// App. A: k = 2c (m2 - m1) (c+d)^(2Ls) / (N(m1) N(m2)), N(m) = b5^Ls + m c5^Ls, 2c = b5 + c5
+double k_of(const eofa_params& p, double m1, double m2) {
+    const double bl = std::pow(p.b, p.Ls), cl = std::pow(p.c, p.Ls);
+    return (p.b + p.c) * (m2 - m1) * bl * bl / ((bl + m1 * cl) * (bl + m2 * cl));
+}
+
+void drop_graphs(eofa_ctx* c) {
+    for (int m = 0; m < 2; ++m)
+        for (int i = 0; i < 4; ++i) {
+            if (c->cg_exec[m][i]) cudaGraphExecDestroy(c->cg_exec[m][i]);
+            if (c->cg_first[m][i]) cudaGraphExecDestroy(c->cg_first[m][i]);
+            c->cg_exec[m][i] = c->cg_first[m][i] = nullptr;
+        }
+}
+
+// Make the context solve H(mh) + beta Delta_pm(ma, mb) P_pm on its lattice
+// and gauge field: new fifth-dimension coefficients.  The captured CG graphs
+// hold the old ones as kernel arguments and the dense comparison matrices
+// are built from them, so both are rebuilt on next use.
+eofa_status set_system(eofa_ctx* c, const eofa_params& np) {
+    if (np.pm != 1 && np.pm != -1) return fail(c, EOFA_ERR_ARG, "pm must be +1 or -1");
+    if (!std::isfinite(np.m1) || !std::isfinite(np.m2) || !std::isfinite(np.m3) || !std::isfinite(np.beta))
+        return fail(c, EOFA_ERR_ARG, "masses and beta must be finite");
+    const eofa_params& o = c->p;
+    if (np.m1 == o.m1 && np.m2 == o.m2 && np.m3 == o.m3 && np.beta == o.beta && np.pm == o.pm) return EOFA_OK;
+    SCoef<double> k64;
+    const char* why = "";
+    eofa_status s = coef_from_params(np, k64, &why);
+    if (s != EOFA_OK) return fail(c, s, why);
+    c->p = np;
+    c->c64 = k64;
+    cast_coef(c->c64, c->c32);
+    drop_graphs(c);
+    c->dense_ready = false;
+    return EOFA_OK;
+}
+
+eofa_status set_system(eofa_ctx* c, double mh, double ma, double mb, double beta, int pm) {
+    eofa_params np = c->p;
+    np.m1 = mh;
+    np.m2 = ma;
+    np.m3 = mb;
+    np.beta = beta;
+    np.pm = pm;
+    return set_system(c, np);
+}
+
+// i-th canonical complex128 5D work field of the action calls
+double* act_buf(eofa_ctx* c, size_t i) {
+    while (c->act5.size() <= i) {
+        void* p = nullptr;
+        if (dalloc(c, &p, (size_t)c->n5 * 2 * 24 * sizeof(double)) != EOFA_OK) return nullptr;
+        c->act5.push_back((double*)p);
+    }
+    return c->act5[i];
+}
+
+bool hard_error(eofa_status s) { return s != EOFA_OK && s != EOFA_ERR_NOT_CONVERGED; }
+
+eofa_status solve_one(eofa_ctx* c, const double* rhs, double* sol, const eofa_solve_opts& o, eofa_solve_stats* stats,
+                      cudaStream_t st) {
+    eofa_status s = solve_impl(c, rhs, sol, o, stats, st);
+    if (stats) stats->status = s;
+    return s;
+}
+
+// Chronological initial guess (Sec. V.B): with the previous solutions psi_k
+// of the same term, x0 = sum_k c_k psi_k where
+// sum_k c_k psi_l^dag A psi_k = psi_l^dag rhs, A the current system (H form);
+// the small system by Gauss-Jordan elimination with partial pivoting.
+// Returns false (no guess) when that system is numerically singular.
+eofa_status forecast(eofa_ctx* c, double* const* prev, int n, const double* rhs, double* guess, bool* used,
+                     cudaStream_t st) {
+    *used = false;
+    if (n < 1) return EOFA_OK;
+    const long nc = c->n5 * 2 * 12;  // complex elements of a 5D field
+    double* w = act_buf(c, 2);
+    if (!w) return EOFA_ERR_OOM;
+    if (!c->mdot) {
+        void* p = nullptr;
+        eofa_status s = dalloc(c, &p, sizeof(double2) * (kMultiBlocks + 1) * kMultiMax);
+        if (s != EOFA_OK) return s;
+        c->mdot = (double*)p;
+    }
+    double* res = c->mdot + 2 * kMultiBlocks * kMultiMax;
+    VecSet set{};
+    set.n = n;
+    for (int l = 0; l < n; ++l) set.v[l] = (const double2*)prev[l];
+    std::vector<double> G(2 * n * n), b(2 * n), tmp(2 * kMultiMax);
+    eofa_status s;
+    for (int k = 0; k <= n; ++k) {
+        const double* rhsk = rhs;
+        if (k < n) {
+            if ((s = apply_impl(c, prev[k], w, 2, st))) return s;
+            rhsk = w;
+        }
+        CK(multidot(set, rhsk, nc, c->mdot, res, st), "multidot");
+        c->launches += 2;
+        CK(cudaMemcpyAsync(tmp.data(), res, sizeof(double2) * n, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+        CK(cudaStreamSynchronize(st), "sync");
+        for (int l = 0; l < n; ++l) {
+            double* dst = k < n ? &G[2 * (l * n + k)] : &b[2 * l];
+            dst[0] = tmp[2 * l];
+            dst[1] = tmp[2 * l + 1];
+        }
+    }
+    // Gauss-Jordan on [G | b], complex entries as (re, im) pairs
+    auto at = [&](int i, int j) -> double* { return &G[2 * (i * n + j)]; };
+    double scale = 0.0;
+    for (int i = 0; i < n * n; ++i) scale = std::max(scale, std::hypot(G[2 * i], G[2 * i + 1]));
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        double best = 0.0;
+        for (int i = col; i < n; ++i) {
+            const double a = std::hypot(at(i, col)[0], at(i, col)[1]);
+            if (a > best) best = a, piv = i;
+        }
+        if (!(best > 1e-13 * scale)) return EOFA_OK;
+        if (piv != col) {
+            for (int j = 0; j < n; ++j) std::swap(at(piv, j)[0], at(col, j)[0]), std::swap(at(piv, j)[1], at(col, j)[1]);
+            std::swap(b[2 * piv], b[2 * col]);
+            std::swap(b[2 * piv + 1], b[2 * col + 1]);
+        }
+        const double pr = at(col, col)[0], pi = at(col, col)[1], d = pr * pr + pi * pi;
+        const double ir = pr / d, ii = -pi / d;  // 1 / pivot
+        for (int j = 0; j < n; ++j) {
+            double* e = at(col, j);
+            const double er = e[0] * ir - e[1] * ii, ei = e[0] * ii + e[1] * ir;
+            e[0] = er, e[1] = ei;
+        }
+        {
+            const double br = b[2 * col] * ir - b[2 * col + 1] * ii, bi = b[2 * col] * ii + b[2 * col + 1] * ir;
+            b[2 * col] = br, b[2 * col + 1] = bi;
+        }
+        for (int i = 0; i < n; ++i) {
+            if (i == col) continue;
+            const double fr = at(i, col)[0], fi = at(i, col)[1];
+            for (int j = 0; j < n; ++j) {
+                const double* r = at(col, j);
+                at(i, j)[0] -= fr * r[0] - fi * r[1];
+                at(i, j)[1] -= fr * r[1] + fi * r[0];
+            }
+            b[2 * i] -= fr * b[2 * col] - fi * b[2 * col + 1];
+            b[2 * i + 1] -= fr * b[2 * col + 1] + fi * b[2 * col];
+        }
+    }
+    for (int l = 0; l < n; ++l) set.c[l] = make_double2(b[2 * l], b[2 * l + 1]);
+    CKL(combine(guess, set, nc, st), "combine");
+    *used = true;
+    return EOFA_OK;
+}
+
+// M_EOFA(m1, m2) phi, Eq. (eofa_action): two H-form solves on the
+// Omega_pm P_pm phi sources; the context's own system is restored by the
+// caller.
+eofa_status meofa_impl(eofa_ctx* c, double m1, double m2, const double* phi, double* out, const eofa_solve_opts& o0,
+                       eofa_solve_stats* stats, cudaStream_t st) {
+    const long V = 2L * c->g.Vh;
+    const int Ls = c->g.Ls;
+    eofa_solve_opts o = o0;
+    o.rhs_form = 0;
+    o.use_guess = 0;
+    double* src = act_buf(c, 0);
+    double* x = act_buf(c, 1);
+    if (!src || !x) return EOFA_ERR_OOM;
+    const double k = k_of(c->p, m1, m2);
+    const OmegaW om_m = omega_of(c->p, -1), om_p = omega_of(c->p, +1);
+    eofa_status s, first = EOFA_OK;
+    // - k P_- Omega_-^dag H(m1)^-1 Omega_- P_- phi
+    if ((s = set_system(c, m1, m1, m2, 0.0, -1))) return s;
+    CKL(omega_in(src, phi, om_m, -1, V, Ls, st), "omega_in");
+    s = solve_one(c, src, x, o, stats ? stats + 0 : nullptr, st);
+    if (hard_error(s)) return s;
+    if (s != EOFA_OK) first = s;
+    CKL(omega_out(out, phi, 1.0, x, om_m, -1, -k, V, Ls, st), "omega_out");
+    // + k P_+ Omega_+^dag [H(m2) - Delta_+(m1, m2) P_+]^-1 Omega_+ P_+ phi
+    if ((s = set_system(c, m2, m1, m2, -1.0, +1))) return s;
+    CKL(omega_in(src, phi, om_p, +1, V, Ls, st), "omega_in");
+    s = solve_one(c, src, x, o, stats ? stats + 1 : nullptr, st);
+    if (hard_error(s)) return s;
+    if (s != EOFA_OK && first == EOFA_OK) first = s;
+    CKL(omega_out(out, out, 1.0, x, om_p, +1, k, V, Ls, st), "omega_out");
+    CK(cudaStreamSynchronize(st), "sync");
+    return first;
+}
+
+// phi = M_EOFA^(-1/2) eta by Eq. (eofa_heatbath): 2 np H-form solves, pole
+// by pole, the minus term then the plus term; with nf > 0 each solve starts
+// from the chronological guess built on the last nf solutions of its own term.
+eofa_status heatbath_impl(eofa_ctx* c, double m1, double m2, int np, const double* alpha, const double* beta,
+                          const double* pole_tol, int nf, const double* eta, double* phi, const eofa_solve_opts& o0,
+                          eofa_solve_stats* stats, cudaStream_t st) {
+    const long V = 2L * c->g.Vh;
+    const int Ls = c->g.Ls;
+    const double k = k_of(c->p, m1, m2);
+    const OmegaW om_m = omega_of(c->p, -1), om_p = omega_of(c->p, +1);
+    double a_tot = alpha[0];
+    for (int l = 0; l < np; ++l) a_tot += alpha[l + 1] / (1.0 + beta[l]);
+    // phi = (alpha_0 + sum_l alpha_l gamma_l) eta, then the 2 np solve terms
+    CKL(omega_out(phi, eta, a_tot, nullptr, om_m, -1, 0.0, V, Ls, st), "omega_out");
+    if (np == 0) {
+        CK(cudaStreamSynchronize(st), "sync");
+        return EOFA_OK;
+    }
+    double* src[2] = {act_buf(c, 0), act_buf(c, 1)};
+    double* x1 = act_buf(c, 3);
+    std::vector<double*> ring[2];
+    for (int t = 0; t < 2; ++t)
+        for (int j = 0; j < nf; ++j) ring[t].push_back(act_buf(c, 4 + t * nf + j));
+    if (!src[0] || !src[1] || !x1) return EOFA_ERR_OOM;
+    for (auto& r : ring)
+        for (double* p : r)
+            if (!p) return EOFA_ERR_OOM;
+    CKL(omega_in(src[0], eta, om_m, -1, V, Ls, st), "omega_in");
+    CKL(omega_in(src[1], eta, om_p, +1, V, Ls, st), "omega_in");
+    eofa_status s, first = EOFA_OK;
+    for (int l = 0; l < np; ++l) {
+        const double g = 1.0 / (1.0 + beta[l]);
+        const double cl = alpha[l + 1] * g * k * g;
+        for (int t = 0; t < 2; ++t) {
+            // t = 0: [H(m1) - gamma_l Delta_-(m1, m2) P_-]^-1, coefficient + alpha_l gamma_l^2 k
+            // t = 1: [H(m2) - beta_l gamma_l Delta_+(m1, m2) P_+]^-1, coefficient - alpha_l gamma_l^2 k
+            if (t == 0) s = set_system(c, m1, m1, m2, -g, -1);
+            else s = set_system(c, m2, m1, m2, -beta[l] * g, +1);
+            if (s) return s;
+            eofa_solve_opts o = o0;
+            o.rhs_form = 0;
+            o.use_guess = 0;
+            if (pole_tol && pole_tol[2 * l + t] > 0.0) o.tol = pole_tol[2 * l + t];
+            double* x = nf ? ring[t][l % nf] : x1;
+            if (nf) {
+                // the previous solutions, oldest first; the slot written now
+                // may still hold the oldest one (combine reads it before the
+                // solve overwrites it)
+                const int have = std::min(l, nf);
+                std::vector<double*> prev;
+                for (int j = l - have; j < l; ++j) prev.push_back(ring[t][j % nf]);
+                bool used = false;
+                if ((s = forecast(c, prev.data(), have, src[t], x, &used, st))) return s;
+                o.use_guess = used ? 1 : 0;
+            }
+            eofa_solve_stats* sp = stats ? stats + 2 * l + t : nullptr;
+            s = solve_one(c, src[t], x, o, sp, st);
+            if (hard_error(s)) return s;
+            if (s != EOFA_OK && first == EOFA_OK) first = s;
+            CKL(omega_out(phi, phi, 1.0, x, t == 0 ? om_m : om_p, t == 0 ? -1 : +1, t == 0 ? cl : -cl, V, Ls, st),
+                "omega_out");
+        }
+    }
+    CK(cudaStreamSynchronize(st), "sync");
+    return first;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1275,6 +1551,51 @@ eofa_status eofa_solve(eofa_ctx* ctx, const void* rhs, void* sol, const eofa_sol
     ctx->err.clear();
     eofa_status s = solve_impl(ctx, (const double*)rhs, (double*)sol, *opts, stats, (cudaStream_t)stream);
     if (stats) stats->status = s;
+    return s;
+}
+
+eofa_status eofa_set_system(eofa_ctx* ctx, double m1, double m2, double m3, double beta, int pm) {
+    if (!ctx) return EOFA_ERR_ARG;
+    ctx->err.clear();
+    return set_system(ctx, m1, m2, m3, beta, pm);
+}
+
+eofa_status eofa_apply_meofa(eofa_ctx* ctx, double m1, double m2, const void* phi, void* out,
+                             const eofa_solve_opts* opts, eofa_solve_stats* stats, void* stream) {
+    if (!ctx || !phi || !out || !opts || phi == out) return EOFA_ERR_ARG;
+    ctx->err.clear();
+    if (!std::isfinite(m1) || !std::isfinite(m2)) return fail(ctx, EOFA_ERR_ARG, "m1, m2 must be finite");
+    if (stats) std::memset(stats, 0, 2 * sizeof(eofa_solve_stats));
+    const eofa_params keep = ctx->p;
+    eofa_status s = meofa_impl(ctx, m1, m2, (const double*)phi, (double*)out, *opts, stats, (cudaStream_t)stream);
+    const std::string why = ctx->err;
+    eofa_status r = set_system(ctx, keep);
+    if (s == EOFA_OK && r != EOFA_OK) return r;
+    ctx->err = why;
+    return s;
+}
+
+eofa_status eofa_heatbath(eofa_ctx* ctx, double m1, double m2, int np, const double* alpha, const double* beta,
+                          const double* pole_tol, int forecast_n, const void* eta, void* phi,
+                          const eofa_solve_opts* opts, eofa_solve_stats* stats, void* stream) {
+    if (!ctx || !eta || !phi || !opts || eta == phi || np < 0 || !alpha || (np > 0 && !beta)) return EOFA_ERR_ARG;
+    ctx->err.clear();
+    if (forecast_n < 0 || forecast_n > kMultiMax)
+        return fail(ctx, EOFA_ERR_ARG, "forecast_n must be in 0.." + std::to_string(kMultiMax));
+    if (!std::isfinite(m1) || !std::isfinite(m2)) return fail(ctx, EOFA_ERR_ARG, "m1, m2 must be finite");
+    for (int l = 0; l <= np; ++l)
+        if (!std::isfinite(alpha[l])) return fail(ctx, EOFA_ERR_ARG, "alpha must be finite");
+    for (int l = 0; l < np; ++l)
+        if (!std::isfinite(beta[l]) || !(beta[l] > -1.0))
+            return fail(ctx, EOFA_ERR_ARG, "every beta_l must be finite and > -1 (gamma_l = 1/(1+beta_l))");
+    if (stats && np > 0) std::memset(stats, 0, 2 * (size_t)np * sizeof(eofa_solve_stats));
+    const eofa_params keep = ctx->p;
+    eofa_status s = heatbath_impl(ctx, m1, m2, np, alpha, beta, pole_tol, forecast_n, (const double*)eta,
+                                  (double*)phi, *opts, stats, (cudaStream_t)stream);
+    const std::string why = ctx->err;
+    eofa_status r = set_system(ctx, keep);
+    if (s == EOFA_OK && r != EOFA_OK) return r;
+    ctx->err = why;
     return s;
 }
 
