@@ -248,6 +248,30 @@ def run_multi_rhs(B, I, torch, dev):
     return out
 
 
+def run_heatbath(B, I, torch, dev, solver):
+    """EOFA heatbath phi = M_EOFA(m1, m2)^(-1/2) eta (Eq. eofa_heatbath) on the
+    benchmark lattice: the largest eigenvalue of M_EOFA by power iteration,
+    the Zolotarev approximation with relative error <= 1e-11 on
+    [0.5, 1.2 lambda_max], then 2 N_p FP32-inner solves to 1e-10 without
+    and with the chronological guess over the last 4 solutions of each term;
+    epsilon of Eq. (heatbath_rel_err) from a further M_EOFA application."""
+    from paper_1706_05843_gb300 import heatbath as H
+    from paper_1706_05843_gb300 import rational
+    a = WORKLOAD["action"]
+    m1, m2 = a["m1"], a["m2"]
+    eta = torch.from_numpy(I.heatbath_noise(WORKLOAD["dims"], 31)).to(dev)
+    lam, _ = H.largest_eigenvalue(solver, m1, m2, eta.clone(), iters=6, tol=1e-8, inner="f32")
+    r = rational.poles_for(1e-11, 0.5, 1.2 * lam)
+    out = {"lambda_max": lam, "interval": [0.5, 1.2 * lam], "poles": r.poles, "approx_err": r.err}
+    for fc in (0, 4):
+        dt, (phi, st) = _timed(torch, lambda: solver.heatbath(eta, m1, m2, r, forecast=fc, tol=TOL, inner="f32"))
+        mphi, _ = solver.apply_meofa(phi, m1, m2, tol=1e-12, inner="f32")
+        out[f"forecast_{fc}"] = {"s": dt, "eps": H.heatbath_error(eta, phi, mphi),
+                                 "inner_iters": [x.inner_iters for x in st],
+                                 "max_true_res": max(x.true_res for x in st)}
+    return out
+
+
 def run_learned(B, I, torch, dev):
     """Learned preconditioner: trained on 2000 (residual, error) pairs from
     16^3x32 Ls=16 solves (gauge seed 3), used in flexible GCR at 32^3x64
@@ -437,6 +461,7 @@ def run_ours(args):
             "cayley": {"s_per_solve": value, "inner_iters": stats[-1]["inner_iters"],
                        "outer": stats[-1]["outer_iters"]},
             "cayley_speedup": dt / value if value else None}
+        workloads["heatbath"] = run_heatbath(B, I, torch, dev, solver)
         solver.close()
         workloads["batched_16rhs_uneven"] = run_batched(B, I, torch, dev)
         workloads["24^3x64_Ls12_4rhs"] = run_multi_rhs(B, I, torch, dev)

@@ -202,3 +202,44 @@ def test_heatbath_arguments(env):
     B.eofa_heatbath(s.ctx, M1, M2, 0.25, [], [], e, phi, opts)
     assert rel(phi.cpu().numpy(), 0.25 * e.cpu().numpy()) < 1e-15
     s.close()
+
+
+def test_largest_eigenvalue_matches_oracle(env):
+    """Power iteration through the library's M_EOFA gives the oracle's
+    Rayleigh quotients, which rise monotonically (M_EOFA is Hermitian
+    positive definite)."""
+    torch, s, a, U = setup(env, CASES[1])
+    from oracle import action as A
+    from paper_1706_05843_gb300 import heatbath as H
+    v0 = I.heatbath_noise(a.dims, 3)
+    lam, hist = H.largest_eigenvalue(s, M1, M2, torch.from_numpy(v0).cuda(), iters=8, tol=1e-12, inner="f32")
+    v = v0 / np.linalg.norm(v0)
+    ref = []
+    for _ in range(8):
+        w, _ = A.meofa(a, U, M1, M2, v)
+        ref.append(np.vdot(v, w).real / np.vdot(v, v).real)
+        v = w / np.linalg.norm(w)
+    assert np.allclose(hist, ref, rtol=1e-9)
+    assert all(x <= y * (1 + 1e-12) for x, y in zip(hist, hist[1:]))
+    s.close()
+
+
+def test_pole_tolerance_tuning(env):
+    """The per-solve tolerance tuning of Sec. V.B keeps epsilon below its
+    target while relaxing tolerances and cutting the iteration count."""
+    torch, s, a, U = setup(env, CASES[0])
+    from paper_1706_05843_gb300 import heatbath as H
+    from paper_1706_05843_gb300 import rational
+    r = rational.poles_for(1e-11, *SPECTRUM)
+    e = torch.from_numpy(I.heatbath_noise(a.dims, 16)).cuda()
+    _, eps0, st0 = H.measure(s, e, M1, M2, r, tol=1e-10, inner="f32")
+    tols, eps, trials = H.tune_pole_tolerances(s, e, M1, M2, r, eps_tol=1e-9, tol=1e-10, factor=100.0,
+                                               max_tol=1e-4, inner="f32")
+    _, eps1, st1 = H.measure(s, e, M1, M2, r, pole_tol=tols, tol=1e-10, inner="f32")
+    it0, it1 = sum(x.inner_iters for x in st0), sum(x.inner_iters for x in st1)
+    print(f"untuned eps {eps0:.3g} {it0} iterations; tuned eps {eps1:.3g} {it1} iterations; "
+          f"{trials} trials; tolerances {tols}")
+    assert eps0 <= 1e-9 and eps1 <= 1e-9
+    assert max(tols) > 1e-10
+    assert it1 < it0
+    s.close()
