@@ -254,7 +254,10 @@ def run_heatbath(B, I, torch, dev, solver):
     the Zolotarev approximation with relative error <= 1e-11 on
     [0.5, 1.2 lambda_max], then 2 N_p FP32-inner solves to 1e-10 without
     and with the chronological guess over the last 4 solutions of each term;
-    epsilon of Eq. (heatbath_rel_err) from a further M_EOFA application."""
+    epsilon of Eq. (heatbath_rel_err) from a further M_EOFA application; then
+    the pseudofermion force at the drawn phi (two solves and the link
+    kernel) with its RMS and largest Frobenius norm over links (Sec. VI
+    force norms)."""
     from paper_1706_05843_gb300 import heatbath as H
     from paper_1706_05843_gb300 import rational
     a = WORKLOAD["action"]
@@ -269,6 +272,11 @@ def run_heatbath(B, I, torch, dev, solver):
         out[f"forecast_{fc}"] = {"s": dt, "eps": H.heatbath_error(eta, phi, mphi),
                                  "inner_iters": [x.inner_iters for x in st],
                                  "max_true_res": max(x.true_res for x in st)}
+    # the pseudofermion force of S = phi^dag M_EOFA phi at the drawn phi (Eq. eofa_force)
+    dt, (f, st) = _timed(torch, lambda: solver.force(phi, m1, m2, tol=TOL, inner="f32"))
+    from paper_1706_05843_gb300.forces import force_norms
+    f_rms, f_max = force_norms(f)
+    out["force"] = {"s": dt, "inner_iters": [x.inner_iters for x in st], "F_RMS": f_rms, "F_max": f_max}
     return out
 
 

@@ -215,6 +215,20 @@ eofa_status eofa_heatbath(eofa_ctx *ctx, double m1, double m2, int np, const dou
                           const void *eta, void *phi, const eofa_solve_opts *opts,
                           eofa_solve_stats *stats, void *stream);
 
+/* EOFA pseudofermion force of S = phi^dag M_EOFA(m1, m2) phi, Sec. III.C
+ * Eq. (eofa_force): with chi_1 = H(m1)^-1 Omega_- P_- phi and
+ * chi_2 = [H(m2) - Delta_+(m1, m2) P_+]^-1 Omega_+ P_+ phi (two H-form
+ * solves),
+ *   d^a S = k (g5 R5 chi_1)^dag (d^a D_W) chi_1 - k (g5 R5 chi_2)^dag (d^a D_W) chi_2,
+ * d^a the derivative along U_mu(x) -> exp(s T^a) U_mu(x) at s = 0,
+ * T^a = i lambda_a / 2 (Tr T^a T^b = -delta^ab / 2).  force: device
+ * complex128 [t][z][y][x][mu][3][3] (the gauge layout) receives
+ * F_mu(x) = sum_a T^a d^a S, anti-Hermitian and traceless.  The links are
+ * the context's own.  stats: NULL or 2 entries (chi_1, chi_2).  Returns
+ * after the work has finished. */
+eofa_status eofa_force(eofa_ctx *ctx, double m1, double m2, const void *phi, void *force,
+                       const eofa_solve_opts *opts, eofa_solve_stats *stats, void *stream);
+
 /* out[i] = K in[i] (dag = 0) or K^dag in[i] (dag = 1) for n contexts,
  * which may have different lattices. */
 eofa_status eofa_apply_batched(eofa_ctx *const *ctx, int n, const void *const *in,

@@ -98,6 +98,8 @@ SIGNATURES = {
     "eofa_set_system": ([_vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int], C.c_int),
     "eofa_apply_meofa": ([_vp, C.c_double, C.c_double, _vp, _vp, C.POINTER(eofa_solve_opts),
                           C.POINTER(eofa_solve_stats), _vp], C.c_int),
+    "eofa_force": ([_vp, C.c_double, C.c_double, _vp, _vp, C.POINTER(eofa_solve_opts),
+                    C.POINTER(eofa_solve_stats), _vp], C.c_int),
     "eofa_heatbath": ([_vp, C.c_double, C.c_double, C.c_int, _dp, _dp, _dp, C.c_int, _vp, _vp,
                        C.POINTER(eofa_solve_opts), C.POINTER(eofa_solve_stats), _vp], C.c_int),
 }
@@ -199,6 +201,14 @@ def eofa_apply_meofa(ctx, m1, m2, phi, out, opts, stream=None, check=True):
     st = (eofa_solve_stats * 2)()
     s = lib().eofa_apply_meofa(ctx, float(m1), float(m2), _dptr(phi), _dptr(out), C.byref(opts), st,
                                _stream(stream))
+    if check:
+        _check(ctx, s)
+    return list(st)
+
+
+def eofa_force(ctx, m1, m2, phi, force, opts, stream=None, check=True):
+    st = (eofa_solve_stats * 2)()
+    s = lib().eofa_force(ctx, float(m1), float(m2), _dptr(phi), _dptr(force), C.byref(opts), st, _stream(stream))
     if check:
         _check(ctx, s)
     return list(st)
@@ -372,6 +382,15 @@ class Solver:
         out = torch.empty(self.shape4, dtype=torch.complex128, device="cuda")
         st = eofa_apply_meofa(self.ctx, m1, m2, phi, out, make_opts(**opts), stream, check)
         return out, st
+
+    def force(self, phi, m1, m2, stream=None, check=True, **opts):
+        """EOFA pseudofermion force sum_a T^a d^a S per link, shape
+        (T, Z, Y, X, 4, 3, 3); returns (force, [chi_1, chi_2] stats)."""
+        import torch
+        X, Y, Z, T = self.dims
+        f = torch.empty((T, Z, Y, X, 4, 3, 3), dtype=torch.complex128, device="cuda")
+        st = eofa_force(self.ctx, m1, m2, phi, f, make_opts(**opts), stream, check)
+        return f, st
 
     def heatbath(self, eta, m1, m2, approx, pole_tol=None, forecast=0, stream=None, check=True, **opts):
         """M_EOFA(m1, m2)^(-1/2) eta with the rational approximation ``approx``

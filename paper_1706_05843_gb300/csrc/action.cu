@@ -2,11 +2,12 @@
 // (Eqs. eofa_action, eofa_heatbath): the maps between the caller's 4D field
 // and the 5D sources and solutions of the H-form solves (Omega_pm P_pm and
 // its adjoint, App. A), and the multi-vector inner products and linear
-// combinations of the chronological initial guess (Sec. V.B).  Fields are in
+// combinations of the chronological initial guess (Sec. V.B), and the
+// pseudofermion force's spin-traced bilinear (Sec. III.C).  Fields are in
 // the caller's canonical complex128 layout ([t][z][y][x][s][spin][colour]
 // for 5D, the same without s for 4D); gamma_5 = diag(1, 1, -1, -1), so
-// P_+ keeps spins 0, 1 and P_- spins 2, 3.  Memory-bound and small next to
-// the solves: one thread per complex element, grid-stride loops.
+// P_+ keeps spins 0, 1 and P_- spins 2, 3.  Small next to the solves: one
+// thread per complex element (per link for the force), grid-stride loops.
 #include "blas.h"
 
 namespace eofa {
@@ -130,6 +131,163 @@ __global__ void __launch_bounds__(AT) k_combine(double2* out, const __grid_const
         }
         out[i] = make_double2(r, m);
     }
+}
+
+// ---------------------------------------------------------------------------
+// EOFA pseudofermion force (Sec. III.C, Eq. eofa_force)
+// ---------------------------------------------------------------------------
+// gamma_mu in the chiral basis has one entry per row:
+// (gamma_mu psi)_alpha = c_{mu,alpha} psi_{perm(mu,alpha)}, c in {+-1, +-i}:
+//   gamma_1: (-i psi3, -i psi2, i psi1, i psi0)   gamma_2: (-psi3, psi2, psi1, -psi0)
+//   gamma_3: (-i psi2, i psi3, i psi0, -i psi1)   gamma_4: (psi2, psi3, psi0, psi1)
+__device__ __forceinline__ double2 gamma_row(int mu, int al, double2 v0, double2 v1, double2 v2, double2 v3) {
+    const int src = mu < 2 ? 3 - al : al ^ 2;
+    const double2 v = src == 0 ? v0 : src == 1 ? v1 : src == 2 ? v2 : v3;
+    const double s03 = (al == 0 || al == 3) ? -1.0 : 1.0;
+    double cr, ci;
+    if (mu == 0) cr = 0.0, ci = al < 2 ? -1.0 : 1.0;
+    else if (mu == 1) cr = s03, ci = 0.0;
+    else if (mu == 2) cr = 0.0, ci = s03;
+    else cr = 1.0, ci = 0.0;
+    return make_double2(cr * v.x - ci * v.y, cr * v.y + ci * v.x);
+}
+
+// M[k][i] += sum_alpha ((1 + sg gamma_mu) b)_{alpha k} conj((gamma_5 a)_{alpha i})
+// for one s: the spin trace of (1 + sg gamma_mu) b a^dag gamma_5 as a colour matrix
+__device__ __forceinline__ void spin_trace(double2 (&M)[3][3], int mu, double sg, const double2* __restrict__ b,
+                                           const double2* __restrict__ a) {
+    double2 av[4][3];
+#pragma unroll
+    for (int al = 0; al < 4; ++al)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double2 v = a[al * 3 + i];
+            av[al][i] = al < 2 ? v : make_double2(-v.x, -v.y);  // gamma_5 = diag(1, 1, -1, -1)
+        }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double2 b0 = b[k], b1 = b[3 + k], b2 = b[6 + k], b3 = b[9 + k];
+#pragma unroll
+        for (int al = 0; al < 4; ++al) {
+            const double2 bb = al == 0 ? b0 : al == 1 ? b1 : al == 2 ? b2 : b3;
+            const double2 g = gamma_row(mu, al, b0, b1, b2, b3);
+            const double pr = bb.x + sg * g.x, pi = bb.y + sg * g.y;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double2 c = av[al][i];  // p * conj(c)
+                M[k][i].x = fma(pr, c.x, fma(pi, c.y, M[k][i].x));
+                M[k][i].y = fma(pi, c.x, fma(-pr, c.y, M[k][i].y));
+            }
+        }
+    }
+}
+
+// One thread per link (x, mu), mu fastest.  For chi_1 (sign +) and chi_2
+// (sign -): M1 = sum_s Tr_spin[(1 - gamma_mu) chi(x+mu, s) (g5 R5 chi)(x, s)^dag],
+// M2 = sum_s Tr_spin[(1 + gamma_mu) chi(x, s) (g5 R5 chi)(x+mu, s)^dag],
+// with (g5 R5 chi)(x, s) = g5 chi(x, Ls-1-s); then
+// Y = -k/2 phase sum_f sign_f (U M1 - M2 U^dag), so that d^a S = Tr(T^a Y), and
+// F = sum_a T^a d^a S = -(1/2) [Y_A - Tr(Y_A)/3], Y_A = (Y - Y^dag)/2, for
+// T^a = i lambda_a / 2.
+__global__ void __launch_bounds__(AT) k_force(const double2* __restrict__ chi1, const double2* __restrict__ chi2,
+                                              const double* __restrict__ l0, const double* __restrict__ l1,
+                                              double2* __restrict__ F, Geom g, double k) {
+    const long t = blockIdx.x * (long)AT + threadIdx.x;
+    const long V = 2L * g.Vh;
+    if (t >= 4 * V) return;
+    const long lex = t >> 2;
+    const int mu = (int)(t & 3);
+    int c[4];
+    {
+        long r = lex;
+        c[0] = (int)(r % g.X); r /= g.X;
+        c[1] = (int)(r % g.Y); r /= g.Y;
+        c[2] = (int)(r % g.Z);
+        c[3] = (int)(r / g.Z);
+    }
+    const int ext = mu == 0 ? g.X : mu == 1 ? g.Y : mu == 2 ? g.Z : g.T;
+    const int cm = mu == 0 ? c[0] : mu == 1 ? c[1] : mu == 2 ? c[2] : c[3];
+    const long stride = mu == 0 ? 1L : mu == 1 ? (long)g.X : mu == 2 ? (long)g.X * g.Y : (long)g.X * g.Y * g.Z;
+    const long nlex = cm + 1 < ext ? lex + stride : lex - (long)(ext - 1) * stride;
+    const double phase = (mu == 3 && cm == ext - 1) ? g.tbc : 1.0;
+    const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+    const double* l = (par ? l1 : l0) + ((lex >> 1) * 4 + mu) * 12;
+    double2 U[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        U[0][j] = make_double2(l[2 * j], l[2 * j + 1]);
+        U[1][j] = make_double2(l[6 + 2 * j], l[6 + 2 * j + 1]);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {  // row 2 = conj(row 0 x row 1)
+        const int p = (j + 1) % 3, q = (j + 2) % 3;
+        const double re = (U[0][p].x * U[1][q].x - U[0][p].y * U[1][q].y) -
+                          (U[0][q].x * U[1][p].x - U[0][q].y * U[1][p].y);
+        const double im = (U[0][p].x * U[1][q].y + U[0][p].y * U[1][q].x) -
+                          (U[0][q].x * U[1][p].y + U[0][q].y * U[1][p].x);
+        U[2][j] = make_double2(re, -im);
+    }
+    const int Ls = g.Ls;
+    double2 Y[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) Y[a][b] = make_double2(0.0, 0.0);
+    for (int f = 0; f < 2; ++f) {
+        const double2* chi = f ? chi2 : chi1;
+        const double2* cx = chi + lex * Ls * 12;
+        const double2* cn = chi + nlex * Ls * 12;
+        double2 M1[3][3], M2[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) M1[a][b] = M2[a][b] = make_double2(0.0, 0.0);
+        for (int s = 0; s < Ls; ++s) {
+            const int sb = Ls - 1 - s;
+            spin_trace(M1, mu, -1.0, cn + s * 12, cx + sb * 12);
+            spin_trace(M2, mu, +1.0, cx + s * 12, cn + sb * 12);
+        }
+        const double sgn = f ? -1.0 : 1.0;
+        // Y += sgn (U M1 - M2 U^dag)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                double re = 0.0, im = 0.0;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    re += U[a][j].x * M1[j][b].x - U[a][j].y * M1[j][b].y;
+                    im += U[a][j].x * M1[j][b].y + U[a][j].y * M1[j][b].x;
+                    // M2[a][j] conj(U[b][j])
+                    re -= M2[a][j].x * U[b][j].x + M2[a][j].y * U[b][j].y;
+                    im -= M2[a][j].y * U[b][j].x - M2[a][j].x * U[b][j].y;
+                }
+                Y[a][b].x += sgn * re;
+                Y[a][b].y += sgn * im;
+            }
+    }
+    const double w = -0.5 * k * phase;
+    // F = -(1/2) [Y_A - Tr(Y_A)/3], Y_A = (Y - Y^dag)/2; Y scaled by w
+    const double trI = w * (Y[0][0].y + Y[1][1].y + Y[2][2].y) / 3.0;  // Im Tr(Y_A) / 3
+    double2* out = F + t * 9;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            double re = 0.5 * w * (Y[a][b].x - Y[b][a].x);
+            double im = 0.5 * w * (Y[a][b].y + Y[b][a].y);
+            if (a == b) im -= trI;
+            out[a * 3 + b] = make_double2(-0.5 * re, -0.5 * im);
+        }
+}
+
+cudaError_t eofa_force_links(const double* chi1, const double* chi2, const void* const links64[2], double* F,
+                             const Geom& g, double k, cudaStream_t st) {
+    const long n = 8L * g.Vh;
+    k_force<<<(int)((n + AT - 1) / AT), AT, 0, st>>>((const double2*)chi1, (const double2*)chi2,
+                                                     (const double*)links64[0], (const double*)links64[1],
+                                                     (double2*)F, g, k);
+    return cudaGetLastError();
 }
 
 cudaError_t omega_in(double* out5, const double* xi4, const OmegaW& om, int chi, long V, int Ls,

@@ -78,5 +78,9 @@ cudaError_t omega_out(double* out4, const double* base4, double a, const double*
 cudaError_t multidot(const VecSet& set, const double* w, long n, double* partial, double* out, cudaStream_t st);
 // out = sum_j set.c[j] set.v[j]
 cudaError_t combine(double* out, const VecSet& set, long n, cudaStream_t st);
+// EOFA force F[lex][mu] (3x3 complex, anti-Hermitian traceless) from the
+// canonical chi_1, chi_2 and the context's FP64 two-row links
+cudaError_t eofa_force_links(const double* chi1, const double* chi2, const void* const links64[2], double* F,
+                             const Geom& g, double k, cudaStream_t st);
 
 }  // namespace eofa

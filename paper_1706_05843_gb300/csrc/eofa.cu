@@ -1393,6 +1393,40 @@ eofa_status meofa_impl(eofa_ctx* c, double m1, double m2, const double* phi, dou
     return first;
 }
 
+// EOFA pseudofermion force, Eq. (eofa_force): chi_1 = H(m1)^-1 Omega_- P_- phi,
+// chi_2 = [H(m2) - Delta_+(m1, m2) P_+]^-1 Omega_+ P_+ phi, then one kernel
+// over the links.  D_EOFA(m) = D_DWF(m) D~(m)^-1 and D_DWF = D_W D~ + (1 - L)
+// make the gauge derivative of D_EOFA that of D_W on every s-slice, for
+// Moebius as for Shamir.
+eofa_status force_impl(eofa_ctx* c, double m1, double m2, const double* phi, double* F, const eofa_solve_opts& o0,
+                       eofa_solve_stats* stats, cudaStream_t st) {
+    const long V = 2L * c->g.Vh;
+    const int Ls = c->g.Ls;
+    eofa_solve_opts o = o0;
+    o.rhs_form = 0;
+    o.use_guess = 0;
+    double* src = act_buf(c, 0);
+    double* chi1 = act_buf(c, 1);
+    double* chi2 = act_buf(c, 3);
+    if (!src || !chi1 || !chi2) return EOFA_ERR_OOM;
+    const double k = k_of(c->p, m1, m2);
+    eofa_status s, first = EOFA_OK;
+    if ((s = set_system(c, m1, m1, m2, 0.0, -1))) return s;
+    CKL(omega_in(src, phi, omega_of(c->p, -1), -1, V, Ls, st), "omega_in");
+    s = solve_one(c, src, chi1, o, stats ? stats + 0 : nullptr, st);
+    if (hard_error(s)) return s;
+    if (s != EOFA_OK) first = s;
+    if ((s = set_system(c, m2, m1, m2, -1.0, +1))) return s;
+    CKL(omega_in(src, phi, omega_of(c->p, +1), +1, V, Ls, st), "omega_in");
+    s = solve_one(c, src, chi2, o, stats ? stats + 1 : nullptr, st);
+    if (hard_error(s)) return s;
+    if (s != EOFA_OK && first == EOFA_OK) first = s;
+    const void* l64[2] = {c->links[EOFA_F64][0], c->links[EOFA_F64][1]};
+    CKL(eofa_force_links(chi1, chi2, l64, F, c->g, k, st), "force");
+    CK(cudaStreamSynchronize(st), "sync");
+    return first;
+}
+
 // phi = M_EOFA^(-1/2) eta by Eq. (eofa_heatbath): 2 np H-form solves, pole
 // by pole, the minus term then the plus term; with nf > 0 each solve starts
 // from the chronological guess built on the last nf solutions of its own term.
@@ -1568,6 +1602,21 @@ eofa_status eofa_apply_meofa(eofa_ctx* ctx, double m1, double m2, const void* ph
     if (stats) std::memset(stats, 0, 2 * sizeof(eofa_solve_stats));
     const eofa_params keep = ctx->p;
     eofa_status s = meofa_impl(ctx, m1, m2, (const double*)phi, (double*)out, *opts, stats, (cudaStream_t)stream);
+    const std::string why = ctx->err;
+    eofa_status r = set_system(ctx, keep);
+    if (s == EOFA_OK && r != EOFA_OK) return r;
+    ctx->err = why;
+    return s;
+}
+
+eofa_status eofa_force(eofa_ctx* ctx, double m1, double m2, const void* phi, void* force,
+                       const eofa_solve_opts* opts, eofa_solve_stats* stats, void* stream) {
+    if (!ctx || !phi || !force || !opts) return EOFA_ERR_ARG;
+    ctx->err.clear();
+    if (!std::isfinite(m1) || !std::isfinite(m2)) return fail(ctx, EOFA_ERR_ARG, "m1, m2 must be finite");
+    if (stats) std::memset(stats, 0, 2 * sizeof(eofa_solve_stats));
+    const eofa_params keep = ctx->p;
+    eofa_status s = force_impl(ctx, m1, m2, (const double*)phi, (double*)force, *opts, stats, (cudaStream_t)stream);
     const std::string why = ctx->err;
     eofa_status r = set_system(ctx, keep);
     if (s == EOFA_OK && r != EOFA_OK) return r;

@@ -243,3 +243,29 @@ def test_pole_tolerance_tuning(env):
     assert max(tols) > 1e-10
     assert it1 < it0
     s.close()
+
+
+FORCE_CASES = [((4, 4, 2, 4), 4, 0.5, {}), CASES[0], CASES[2]]
+FORCE_IDS = ["4x4x2x4_Ls4", IDS[0], IDS[2]]
+
+
+@pytest.mark.parametrize("case", FORCE_CASES, ids=FORCE_IDS)
+@pytest.mark.parametrize("inner", ["f64", "f32"])
+def test_force_parity(env, case, inner):
+    """The EOFA force (Eq. eofa_force) per link against the oracle's, whose
+    closed form is pinned to finite differences of the action."""
+    torch, s, a, U = setup(env, case)
+    from oracle import force as F
+    phi = I.heatbath_noise(a.dims, 21)
+    f, st = s.force(torch.from_numpy(phi).cuda(), M1, M2, tol=1e-12, inner=inner)
+    assert all(x.status == 0 for x in st)
+    dS, Fo, imag, _ = F.eofa_force(a, U, M1, M2, phi)
+    f = f.cpu().numpy()
+    assert rel(f, Fo) < 1e-9
+    # anti-Hermitian and traceless
+    assert np.abs(f + np.swapaxes(f, -1, -2).conj()).max() < 1e-14 * np.abs(f).max() + 1e-300
+    assert np.abs(np.trace(f, axis1=-2, axis2=-1)).max() < 1e-13 * np.abs(f).max()
+    # d^a S = -2 Tr(T^a F) recovers the oracle's derivatives
+    dS_gpu = -2.0 * np.einsum("aij,...ji->...a", F.generators(), f).real
+    assert np.abs(dS_gpu - dS).max() < 1e-9 * np.abs(dS).max()
+    s.close()

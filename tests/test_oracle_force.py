@@ -70,3 +70,15 @@ def test_force_matches_finite_differences(oracle_mod, setup, site, mu, gen):
     an = dS[t, z, y, x, mu, gen]
     scale = np.abs(dS).max()
     assert abs(fd - an) < 1e-6 * scale + 1e-6 * abs(an), (fd, an, scale)
+
+
+def test_force_norms(setup):
+    """||F_mu(x)|| of Sec. VI from the matrix form equals the generator
+    components' Euclidean norm; F_RMS and F_max as printed."""
+    from paper_1706_05843_gb300.forces import force_norms, link_norms
+    a, U, phi, dS, Fm, imag, st = setup
+    ref = np.sqrt(np.sum(dS ** 2, axis=-1))
+    assert np.allclose(link_norms(Fm), ref, rtol=1e-13)
+    rms, mx = force_norms(Fm)
+    assert abs(rms - np.sqrt(np.sum(ref ** 2)) / ref.size) < 1e-13 * rms
+    assert mx == pytest.approx(ref.max(), rel=1e-13)
