@@ -280,6 +280,23 @@ def run_heatbath(B, I, torch, dev, solver):
     return out
 
 
+def run_gparity(B, I, torch, dev):
+    """G-parity boundary conditions in x, y and z (Sec. I) on the benchmark
+    lattice and action: the two-flavour system (FP32 inner, FP64
+    correction, 1e-10), one warm-up solve then one timed solve."""
+    w = WORKLOAD
+    U = torch.from_numpy(I.gauge_field(w["dims"], w["eps"], w["gauge_seed"])).to(dev)
+    s = B.Solver(U, w["dims"], w["Ls"], gparity=7, **w["action"])
+    del U
+    rhs = torch.from_numpy(np.stack([I.gaussian_fermion(w["dims"], w["Ls"], 1001 + i) for i in (0, 1)])).to(dev)
+    sol = torch.empty_like(rhs)
+    s.solve(rhs, out=sol, tol=TOL, inner="f32")
+    dt, (_, st) = _timed(torch, lambda: s.solve(rhs, out=sol, tol=TOL, inner="f32"))
+    s.close()
+    return {"gparity_dirs": "xyz", "flavours": 2, "s_per_solve": dt, "inner_iters": st.inner_iters,
+            "outer": st.outer_iters, "true_res": st.true_res, "status": st.status}
+
+
 def run_learned(B, I, torch, dev):
     """Learned preconditioner: trained on 2000 (residual, error) pairs from
     16^3x32 Ls=16 solves (gauge seed 3), used in flexible GCR at 32^3x64
@@ -471,6 +488,7 @@ def run_ours(args):
             "cayley_speedup": dt / value if value else None}
         workloads["heatbath"] = run_heatbath(B, I, torch, dev, solver)
         solver.close()
+        workloads["gparity_xyz"] = run_gparity(B, I, torch, dev)
         workloads["batched_16rhs_uneven"] = run_batched(B, I, torch, dev)
         workloads["24^3x64_Ls12_4rhs"] = run_multi_rhs(B, I, torch, dev)
         if args.learned:

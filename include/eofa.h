@@ -137,6 +137,23 @@ typedef struct eofa_ctx eofa_ctx;
 eofa_status eofa_create(const eofa_params *p, const void *gauge, void *stream,
                         eofa_ctx **out);
 
+/* Create a context with G-parity boundary conditions (Sec. I): the light
+ * doublet maps as (u, d) -> (d-bar, -u-bar) across the boundary of every
+ * direction mu with bit mu of gparity_dirs set (1..15; bit 0 = x ... bit 3 =
+ * t).  The operator acts on two flavours, psi_1 = u and psi_2 = C d-bar^T:
+ * flavour 2 sees the conjugate links U*, and a hop across a G-parity
+ * boundary changes flavour with psi_1(x + L mu^) = psi_2(x) and
+ * psi_2(x + L mu^) = -psi_1(x); t_bc multiplies hops across the t boundary
+ * as before.  p->dims and gauge are the physical lattice and links.
+ * Every field of this context holds both flavours stacked along t:
+ * 5D [f][t][z][y][x][s][spin][colour] and 4D [f][t][z][y][x][spin][colour],
+ * twice the single-flavour size; internally the context is the
+ * single-flavour solver on X x Y x Z x 2T, so every call (solve, action,
+ * heatbath, force) works unchanged.  eofa_force returns the force on the
+ * physical links (flavour 1's link plus the conjugate of flavour 2's). */
+eofa_status eofa_create_gparity(const eofa_params *p, const void *gauge, int gparity_dirs,
+                                void *stream, eofa_ctx **out);
+
 /* out = K in, K = D_DWF(m1) + pm beta u_pm (x) v_pm P_pm (App. B).
  * in, out: device complex128 5D fields; in != out. */
 eofa_status eofa_apply(eofa_ctx *ctx, const void *in, void *out, void *stream);

@@ -76,6 +76,7 @@ _fp = C.POINTER(C.c_float)
 _dp = C.POINTER(C.c_double)
 SIGNATURES = {
     "eofa_create": ([C.POINTER(eofa_params), _vp, _vp, C.POINTER(_vp)], C.c_int),
+    "eofa_create_gparity": ([C.POINTER(eofa_params), _vp, C.c_int, _vp, C.POINTER(_vp)], C.c_int),
     "eofa_apply": ([_vp, _vp, _vp, _vp], C.c_int),
     "eofa_apply_dag": ([_vp, _vp, _vp, _vp], C.c_int),
     "eofa_apply_h": ([_vp, _vp, _vp, _vp], C.c_int),
@@ -170,6 +171,13 @@ def make_opts(tol=1e-10, inner="f64", inner_tol=0.0, max_iter=0, max_outer=0, us
 def eofa_create(params, gauge, stream=None):
     ctx = C.c_void_p()
     _check(None, lib().eofa_create(C.byref(params), _dptr(gauge), _stream(stream), C.byref(ctx)))
+    return ctx
+
+
+def eofa_create_gparity(params, gauge, gparity_dirs, stream=None):
+    ctx = C.c_void_p()
+    _check(None, lib().eofa_create_gparity(C.byref(params), _dptr(gauge), int(gparity_dirs), _stream(stream),
+                                           C.byref(ctx)))
     return ctx
 
 
@@ -331,20 +339,29 @@ def eofa_hop_bytes(ctx, prec, with_local):
 
 
 class Solver:
-    """Context owner: Solver(gauge, dims, Ls, **action) then apply / solve."""
+    """Context owner: Solver(gauge, dims, Ls, **action) then apply / solve.
+    gparity: 0, or the bit mask of G-parity directions (bit 0 = x .. bit 3 =
+    t); fields then carry a leading flavour axis of 2."""
 
-    def __init__(self, gauge, dims, Ls, stream=None, **action):
+    def __init__(self, gauge, dims, Ls, stream=None, gparity=0, **action):
         import torch
         if isinstance(gauge, np.ndarray):
             gauge = torch.from_numpy(np.ascontiguousarray(gauge)).cuda()
         self.params = make_params(dims, Ls, **action)
-        self.dims, self.Ls = tuple(dims), int(Ls)
-        self.ctx = eofa_create(self.params, gauge, stream)
+        self.dims, self.Ls, self.gparity = tuple(dims), int(Ls), int(gparity)
+        if self.gparity:
+            self.ctx = eofa_create_gparity(self.params, gauge, self.gparity, stream)
+        else:
+            self.ctx = eofa_create(self.params, gauge, stream)
+
+    @property
+    def _flavours(self):
+        return (2,) if self.gparity else ()
 
     @property
     def shape5(self):
         X, Y, Z, T = self.dims
-        return (T, Z, Y, X, self.Ls, 4, 3)
+        return self._flavours + (T, Z, Y, X, self.Ls, 4, 3)
 
     def _new(self):
         import torch
@@ -371,7 +388,7 @@ class Solver:
     @property
     def shape4(self):
         X, Y, Z, T = self.dims
-        return (T, Z, Y, X, 4, 3)
+        return self._flavours + (T, Z, Y, X, 4, 3)
 
     def set_system(self, m1, m2, m3, beta, pm):
         eofa_set_system(self.ctx, m1, m2, m3, beta, pm)

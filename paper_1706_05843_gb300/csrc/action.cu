@@ -203,14 +203,23 @@ __global__ void __launch_bounds__(AT) k_force(const double2* __restrict__ chi1, 
         c[0] = (int)(r % g.X); r /= g.X;
         c[1] = (int)(r % g.Y); r /= g.Y;
         c[2] = (int)(r % g.Z);
-        c[3] = (int)(r / g.Z);
+        c[3] = (int)(r / g.Z);  // t + f Tp (flavour f of a G-parity context)
     }
-    const int ext = mu == 0 ? g.X : mu == 1 ? g.Y : mu == 2 ? g.Z : g.T;
+    const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+    const int f = c[3] >= g.Tp ? 1 : 0;
+    c[3] -= f * g.Tp;
+    const int ext = mu == 0 ? g.X : mu == 1 ? g.Y : mu == 2 ? g.Z : g.Tp;
     const int cm = mu == 0 ? c[0] : mu == 1 ? c[1] : mu == 2 ? c[2] : c[3];
     const long stride = mu == 0 ? 1L : mu == 1 ? (long)g.X : mu == 2 ? (long)g.X * g.Y : (long)g.X * g.Y * g.Z;
-    const long nlex = cm + 1 < ext ? lex + stride : lex - (long)(ext - 1) * stride;
-    const double phase = (mu == 3 && cm == ext - 1) ? g.tbc : 1.0;
-    const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+    const bool cross = cm + 1 == ext;
+    long nlex = cross ? lex - (long)(ext - 1) * stride : lex + stride;
+    bool neg = cross && ((g.apmask >> mu) & 1);
+    if (cross && ((g.gpmask >> mu) & 1)) {
+        // G-parity: psi_1(x + L) = psi_2(x), psi_2(x + L) = -psi_1(x)
+        nlex += (long)(1 - 2 * f) * g.Tp * g.X * g.Y * g.Z;
+        neg = neg != (f == 1);
+    }
+    const double phase = neg ? -1.0 : 1.0;
     const double* l = (par ? l1 : l0) + ((lex >> 1) * 4 + mu) * 12;
     double2 U[3][3];
 #pragma unroll
@@ -279,6 +288,22 @@ __global__ void __launch_bounds__(AT) k_force(const double2* __restrict__ chi1, 
             if (a == b) im -= trI;
             out[a * 3 + b] = make_double2(-0.5 * re, -0.5 * im);
         }
+}
+
+// G-parity: the force on the physical link U_mu(x) is the stacked lattice's
+// force on flavour 1's copy plus the conjugate of that on flavour 2's copy
+// (flavour 2 carries conj(U), and conj(exp(s T^a) U) = exp(s conj(T^a)) conj(U))
+__global__ void __launch_bounds__(AT) k_force_fold(const double2* __restrict__ Fs, double2* __restrict__ F,
+                                                   long n) {
+    const long i = blockIdx.x * (long)AT + threadIdx.x;
+    if (i >= n) return;
+    const double2 a = Fs[i], b = Fs[n + i];
+    F[i] = make_double2(a.x + b.x, a.y - b.y);
+}
+
+cudaError_t force_fold(const double* Fs, double* F, long n, cudaStream_t st) {
+    k_force_fold<<<(int)((n + AT - 1) / AT), AT, 0, st>>>((const double2*)Fs, (double2*)F, n);
+    return cudaGetLastError();
 }
 
 cudaError_t eofa_force_links(const double* chi1, const double* chi2, const void* const links64[2], double* F,

@@ -451,6 +451,22 @@ cudaError_t gauge_import(const double* U, const Geom& g, void* const links[4][2]
     return cudaGetLastError();
 }
 
+// G-parity: the flavour-stacked gauge field [U; U*] (flavour 2 carries the
+// conjugate links) from the physical U, n = complex entries of U
+__global__ void __launch_bounds__(BT) k_gparity_gauge(const double2* __restrict__ U, double2* __restrict__ out,
+                                                      long n) {
+    const long i = (long)blockIdx.x * BT + threadIdx.x;
+    if (i >= n) return;
+    const double2 u = U[i];
+    out[i] = u;
+    out[n + i] = make_double2(u.x, -u.y);
+}
+
+cudaError_t gparity_gauge(const double* U, double* out, long n, cudaStream_t st) {
+    k_gparity_gauge<<<grid_for(n), BT, 0, st>>>((const double2*)U, (double2*)out, n);
+    return cudaGetLastError();
+}
+
 int blas_max_grid(long n5) { return grid_for(n5); }
 
 // ===========================================================================

@@ -45,6 +45,8 @@ cudaError_t blas_zero(int prec, VecRef v, long n5, int Ls, cudaStream_t st);
 cudaError_t layout_import(VecRef dst, const double* src, const Geom& g, int par, int g5r5, cudaStream_t st);
 cudaError_t layout_export(double* dst, VecRef src, const Geom& g, int par, int g5r5, cudaStream_t st);
 cudaError_t gauge_import(const double* U, const Geom& g, void* const links[4][2], int* bad, cudaStream_t st);
+// [U; conj(U)] for a G-parity context (n complex entries of U)
+cudaError_t gparity_gauge(const double* U, double* out, long n, cudaStream_t st);
 int blas_max_grid(long n5);
 
 // learned preconditioner support (FP32 odd-parity fields <-> network activations)
@@ -82,5 +84,7 @@ cudaError_t combine(double* out, const VecSet& set, long n, cudaStream_t st);
 // canonical chi_1, chi_2 and the context's FP64 two-row links
 cudaError_t eofa_force_links(const double* chi1, const double* chi2, const void* const links64[2], double* F,
                              const Geom& g, double k, cudaStream_t st);
+// G-parity: F = Fs[flavour 1] + conj(Fs[flavour 2]), n = complex entries of F
+cudaError_t force_fold(const double* Fs, double* F, long n, cudaStream_t st);
 
 }  // namespace eofa

@@ -29,8 +29,13 @@ struct Geom {
     int Xh;      // X / 2
     int Vh;      // 4D sites per parity
     int Ls;
-    int pad;
-    double tbc;  // +1 periodic / -1 antiperiodic time
+    int apmask;  // bit mu set: hops across the mu boundary carry a factor -1
+    // G-parity (Sec. I): bit mu set for a G-parity direction.  The two
+    // flavours are stacked along t (T = 2 Tp, flavour f at t + f Tp); a hop
+    // across a G-parity boundary changes flavour, psi_1(x + L) = psi_2(x),
+    // psi_2(x + L) = -psi_1(x); flavour 2 carries the conjugate links.
+    int gpmask;
+    int Tp;      // physical time extent (T without G-parity)
 };
 
 // Fifth-dimension coefficients of one context, in compute precision R.

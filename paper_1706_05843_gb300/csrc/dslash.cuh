@@ -698,8 +698,9 @@ __device__ __forceinline__ void hop_body(const HopArgs& a, const SCoef<typename 
 
     // ---------------- phase 0: links and neighbours, once per 4D site ---
     // The 8 links of each site (4 forward from this parity, 4 backward from
-    // the neighbours) and the 8 neighbour indices (bit 31: the hop crosses
-    // the time boundary) for all Ls slices of the site.  Issue: indices and
+    // the neighbours) and the 8 neighbour indices (bit 31: the hop carries a
+    // factor -1, from an antiperiodic or a G-parity boundary) for all Ls
+    // slices of the site.  Issue: indices and
     // cp.async of the raw records; finish: the third row rebuilt.
     auto stage_issue = [&](long blk, int b) {
         for (int j = tid; j < NL; j += NT) {
@@ -710,15 +711,24 @@ __device__ __forceinline__ void hop_body(const HopArgs& a, const SCoef<typename 
                 const int xh = rem % g.Xh; rem /= g.Xh;
                 const int y = rem % g.Y; rem /= g.Y;
                 const int z = rem % g.Z;
-                const int t = rem / g.Z;
-                const int x = 2 * xh + ((a.out_par + y + z + t) & 1);
+                const int tf = rem / g.Z;  // t + f Tp for flavour f (G-parity), else t
+                const int x = 2 * xh + ((a.out_par + y + z + tf) & 1);
+                const int f = tf >= g.Tp ? 1 : 0;
                 // step in direction mu (forward for d < 4), periodic wrap
-                const int c = mu == 0 ? x : mu == 1 ? y : mu == 2 ? z : t;
-                const int e = mu == 0 ? g.X : mu == 1 ? g.Y : mu == 2 ? g.Z : g.T;
-                const int n = (d < 4) ? (c + 1 == e ? 0 : c + 1) : (c == 0 ? e - 1 : c - 1);
-                const unsigned edge = (mu == 3 && (d < 4 ? t == g.T - 1 : t == 0)) ? 0x80000000u : 0u;
-                const long ncb = ((((long)(mu == 3 ? n : t) * g.Z + (mu == 2 ? n : z)) * g.Y + (mu == 1 ? n : y)) *
-                                      g.X + (mu == 0 ? n : x)) >> 1;
+                const int c = mu == 0 ? x : mu == 1 ? y : mu == 2 ? z : tf - f * g.Tp;
+                const int e = mu == 0 ? g.X : mu == 1 ? g.Y : mu == 2 ? g.Z : g.Tp;
+                const bool cross = (d < 4) ? (c + 1 == e) : (c == 0);
+                const int n = (d < 4) ? (cross ? 0 : c + 1) : (cross ? e - 1 : c - 1);
+                long ncb = ((((long)(mu == 3 ? n + f * g.Tp : tf) * g.Z + (mu == 2 ? n : z)) * g.Y +
+                             (mu == 1 ? n : y)) * g.X + (mu == 0 ? n : x)) >> 1;
+                bool neg = cross && ((g.apmask >> mu) & 1);
+                if (cross && ((g.gpmask >> mu) & 1)) {
+                    // G-parity boundary: psi_1(x + L) = psi_2(x), psi_2(x + L) = -psi_1(x);
+                    // the other flavour is half the stacked lattice away
+                    ncb += f ? -(long)(g.Vh / 2) : (long)(g.Vh / 2);
+                    neg = neg != ((d < 4) ? f == 1 : f == 0);
+                }
+                const unsigned edge = neg ? 0x80000000u : 0u;
                 snb[b * NL + j] = (unsigned)ncb | edge;
                 const long site = (d < 4) ? jcb : ncb;
                 const unsigned char* src = reinterpret_cast<const unsigned char*>(d < 4 ? a.lk_out : a.lk_in) +
@@ -745,8 +755,11 @@ __device__ __forceinline__ void hop_body(const HopArgs& a, const SCoef<typename 
                 if constexpr (LinkRaw<S>::SEP) link_from_raw<S, R>(sraw + (b * NL + j) * RAWB, u);
                 else link_from_raw<S, R>(reinterpret_cast<const unsigned char*>(dl), u);
                 rebuild_row2(u);
+                // the factor -1 of an antiperiodic or G-parity boundary hop
+                // in x, y, z rides on the staged link (t: applied in the hop)
+                const R sg = ((j & 3) != 3 && (snb[b * NL + j] >> 31)) ? (R)-1 : (R)1;
 #pragma unroll
-                for (int i = 0; i < 18; ++i) dl[i] = u[i];
+                for (int i = 0; i < 18; ++i) dl[i] = sg * u[i];
             }
         }
     };
@@ -790,7 +803,8 @@ __device__ __forceinline__ void hop_body(const HopArgs& a, const SCoef<typename 
                     for (int dir = 0; dir < 2; ++dir) {
                         const unsigned nb = snc[il * 8 + dir * 4 + mu];
                         const long ncb = (long)(nb & 0x7fffffffu);
-                        const R ph = (mu == 3 && (nb >> 31)) ? (R)g.tbc : (R)1;
+                        // the t boundary's sign; x, y, z signs ride on the staged links
+                        const R ph = (mu == 3 && (nb >> 31)) ? (R)-1 : (R)1;
                         R p[24];
                         load_sp<S, R>(a.in, a.in_nrm, ncb, s, LS, p);
                         if constexpr (KT::PRE) {

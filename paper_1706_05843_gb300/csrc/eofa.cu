@@ -1422,7 +1422,16 @@ eofa_status force_impl(eofa_ctx* c, double m1, double m2, const double* phi, dou
     if (hard_error(s)) return s;
     if (s != EOFA_OK && first == EOFA_OK) first = s;
     const void* l64[2] = {c->links[EOFA_F64][0], c->links[EOFA_F64][1]};
-    CKL(eofa_force_links(chi1, chi2, l64, F, c->g, k, st), "force");
+    if (c->g.gpmask) {
+        // the stacked lattice's force (2 V links) in a work field, folded
+        // onto the physical links
+        double* Fs = act_buf(c, 2);
+        if (!Fs) return EOFA_ERR_OOM;
+        CKL(eofa_force_links(chi1, chi2, l64, Fs, c->g, k, st), "force");
+        CKL(force_fold(Fs, F, V / 2 * 4 * 9, st), "force fold");
+    } else {
+        CKL(eofa_force_links(chi1, chi2, l64, F, c->g, k, st), "force");
+    }
     CK(cudaStreamSynchronize(st), "sync");
     return first;
 }
@@ -1501,7 +1510,9 @@ eofa_status heatbath_impl(eofa_ctx* c, double m1, double m2, int np, const doubl
 // ===========================================================================
 extern "C" {
 
-eofa_status eofa_create(const eofa_params* p, const void* gauge, void* stream, eofa_ctx** out) {
+// gpmask = 0: the single-flavour lattice of p; otherwise G-parity in the
+// directions of gpmask with the two flavours stacked along t
+static eofa_status create_impl(const eofa_params* p, const void* gauge, int gpmask, void* stream, eofa_ctx** out) {
     if (!out) return EOFA_ERR_ARG;
     *out = nullptr;
     if (!p || !gauge) return EOFA_ERR_ARG;
@@ -1514,14 +1525,16 @@ eofa_status eofa_create(const eofa_params* p, const void* gauge, void* stream, e
     if (!c) return EOFA_ERR_OOM;
     c->p = *p;
     Geom& g = c->g;
-    g.X = p->dims[0]; g.Y = p->dims[1]; g.Z = p->dims[2]; g.T = p->dims[3];
+    g.X = p->dims[0]; g.Y = p->dims[1]; g.Z = p->dims[2];
+    g.Tp = p->dims[3];
+    g.T = gpmask ? 2 * g.Tp : g.Tp;
+    g.gpmask = gpmask;
     g.Xh = g.X / 2;
     const long V = (long)g.X * g.Y * g.Z * g.T;
     if (V / 2 > (1L << 30)) { delete c; return EOFA_ERR_UNSUPPORTED; }
     g.Vh = (int)(V / 2);
     g.Ls = p->Ls;
-    g.pad = 0;
-    g.tbc = (double)p->t_bc;
+    g.apmask = p->t_bc == -1 ? 8 : 0;
     c->n5 = (long)g.Vh * g.Ls;
     eofa_status s = build_coef(c);
     cudaStream_t st = (cudaStream_t)stream;
@@ -1553,8 +1566,23 @@ eofa_status eofa_create(const eofa_params* p, const void* gauge, void* stream, e
         (e = cudaMemsetAsync(c->d_flag, 0, 256, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->scal, 0, sizeof(DevScal), st)) != cudaSuccess)
         return bail(cuda_fail(c, e, "memset"));
-    if ((e = gauge_import((const double*)gauge, g, c->links, c->d_flag, st)) != cudaSuccess)
-        return bail(cuda_fail(c, e, "gauge import"));
+    void* stacked = nullptr;  // G-parity: [U; U*], freed once imported
+    if (gpmask) {
+        const long n = (V / 2) * 4 * 9;  // complex entries of the physical U
+        if ((e = cudaMalloc(&stacked, (size_t)n * 2 * 2 * sizeof(double))) != cudaSuccess)
+            return bail(cuda_fail(c, e, "cudaMalloc"));
+        if ((e = gparity_gauge((const double*)gauge, (double*)stacked, n, st)) != cudaSuccess) {
+            cudaFree(stacked);
+            return bail(cuda_fail(c, e, "G-parity gauge"));
+        }
+    }
+    e = gauge_import(stacked ? (const double*)stacked : (const double*)gauge, g, c->links, c->d_flag, st);
+    if (stacked) {
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        cudaFree(stacked);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e != cudaSuccess) return bail(cuda_fail(c, e, "gauge import"));
     int bad = 0;
     if ((e = cudaMemcpyAsync(&bad, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
@@ -1562,6 +1590,17 @@ eofa_status eofa_create(const eofa_params* p, const void* gauge, void* stream, e
     if (bad) return bail(EOFA_ERR_ARG);
     *out = c;
     return EOFA_OK;
+}
+
+eofa_status eofa_create(const eofa_params* p, const void* gauge, void* stream, eofa_ctx** out) {
+    return create_impl(p, gauge, 0, stream, out);
+}
+
+eofa_status eofa_create_gparity(const eofa_params* p, const void* gauge, int gparity_dirs, void* stream,
+                                eofa_ctx** out) {
+    if (out) *out = nullptr;
+    if (gparity_dirs < 1 || gparity_dirs > 15) return EOFA_ERR_ARG;
+    return create_impl(p, gauge, gparity_dirs, stream, out);
 }
 
 eofa_status eofa_apply(eofa_ctx* ctx, const void* in, void* out, void* stream) {
@@ -1817,8 +1856,9 @@ extern "C" eofa_status eofa_apply_noalloc(const eofa_params* p, const void* gaug
     g.Xh = g.X / 2;
     g.Vh = (int)(V / 2);
     g.Ls = p->Ls;
-    g.pad = 0;
-    g.tbc = (double)p->t_bc;
+    g.apmask = p->t_bc == -1 ? 8 : 0;
+    g.gpmask = 0;
+    g.Tp = g.T;
     void* links[4][2];
     size_t off = 0;
     for (int pr = 0; pr < 4; ++pr)
