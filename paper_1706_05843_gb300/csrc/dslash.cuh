@@ -756,10 +756,14 @@ __device__ __forceinline__ void hop_body(const HopArgs& a, const SCoef<typename 
                 else link_from_raw<S, R>(reinterpret_cast<const unsigned char*>(dl), u);
                 rebuild_row2(u);
                 // the factor -1 of an antiperiodic or G-parity boundary hop
-                // in x, y, z rides on the staged link (t: applied in the hop)
-                const R sg = ((j & 3) != 3 && (snb[b * NL + j] >> 31)) ? (R)-1 : (R)1;
+                // in x, y, z rides on the staged link (t: applied in the hop);
+                // the branch is uniform over the grid
+                if ((g.gpmask | (g.apmask & 7)) && (j & 3) != 3 && (snb[b * NL + j] >> 31)) {
 #pragma unroll
-                for (int i = 0; i < 18; ++i) dl[i] = sg * u[i];
+                    for (int i = 0; i < 18; ++i) u[i] = -u[i];
+                }
+#pragma unroll
+                for (int i = 0; i < 18; ++i) dl[i] = u[i];
             }
         }
     };
