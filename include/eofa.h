@@ -36,7 +36,7 @@
  *  - Gamma matrices in the chiral basis: gamma_k = [[0,-i sigma_k],[i sigma_k,0]],
  *    gamma_4 = [[0,1],[1,0]], gamma_5 = diag(1,1,-1,-1); P_pm = (1 pm gamma_5)/2.
  *  - Hops across the t boundary carry t_bc (-1: antiperiodic); space is
- *    periodic.
+ *    periodic, except in the G-parity directions of eofa_create_gparity.
  *  - Ownership: all field pointers belong to the caller and are not kept
  *    after a call returns.  eofa_create copies the gauge field into the
  *    context (compressed, even-odd blocked); the context owns its device
@@ -190,7 +190,7 @@ eofa_status eofa_solve(eofa_ctx *ctx, const void *rhs, void *sol,
  * leaves its best iterate in the result and its status in stats; the call
  * then returns EOFA_ERR_NOT_CONVERGED after finishing every solve.  Any
  * other failing status stops the call.  The calls allocate canonical 5D work
- * fields (three plus two per forecast vector, 24 * Ls * X*Y*Z*T doubles
+ * fields (up to four plus two per forecast vector, 24 * Ls * X*Y*Z*T doubles
  * each) in the context on first use and keep them until eofa_destroy.
  * ------------------------------------------------------------------------- */
 
