@@ -70,3 +70,17 @@ def test_argument_errors_without_gpu(libeofa):
     assert libeofa.eofa_create(C.byref(p), None, None, C.byref(ctx)) == 1
     assert libeofa.eofa_apply(None, None, None, None) == 1
     assert libeofa.eofa_solve(None, None, None, None, None, None) == 1
+    # G-parity: the direction mask must name 1..4 directions; the same
+    # parameter checks as eofa_create
+    p = B.make_params((4, 4, 4, 4), 8)
+    for dirs in (0, 16, -1):
+        assert libeofa.eofa_create_gparity(C.byref(p), C.c_void_p(1), dirs, None, C.byref(ctx)) == 1
+    p = B.make_params((4, 4, 4, 3), 8)
+    assert libeofa.eofa_create_gparity(C.byref(p), C.c_void_p(1), 1, None, C.byref(ctx)) == 1
+    # action calls without a context
+    opts = B.make_opts(tol=1e-10)
+    assert libeofa.eofa_set_system(None, 0.04, 1.0, 0.04, -1.0, 1) == 1
+    assert libeofa.eofa_apply_meofa(None, 0.04, 1.0, None, None, C.byref(opts), None, None) == 1
+    assert libeofa.eofa_force(None, 0.04, 1.0, None, None, C.byref(opts), None, None) == 1
+    assert libeofa.eofa_heatbath(None, 0.04, 1.0, 0, None, None, None, 0, None, None, C.byref(opts), None,
+                                 None) == 1
