@@ -345,6 +345,33 @@ def test_meofa_apply_matches_dense(oracle_mod, dense24):
     assert rel(out.reshape(-1), M @ eta.reshape(-1)) < 1e-10
 
 
+@pytest.mark.parametrize("coef", [MOBIUS2, SHAMIR], ids=["b1.4_c0.8", "shamir"])
+def test_m_eofa_other_kernels(oracle_mod, coef):
+    """For b - c != 1 and for Shamir (c = d = 1/2) the App. A closed forms of
+    k and Omega_pm still give det D_EOFA(m1) / det D_EOFA(m2) = 1 / det M_EOFA
+    with M_EOFA Hermitian positive definite, and the oracle's two-solve
+    M_EOFA phi equals the dense one."""
+    from oracle import action as A
+    O = oracle_mod
+    dims, Ls, m1, m2 = (2, 2, 2, 2), 4, 0.04, 1.0
+    o = O.Oracle(O.Action(dims=dims, Ls=Ls, m1=m1, m2=m2, m3=m1, **coef), I.gauge_field(dims, 0.5, 2))
+    n = 16 * Ls * 12
+    d = dict(o=o, n=n, V=16, Ls=Ls, m1=m1, m2=m2)
+    d["H1"] = assemble(lambda v: o.h(v, m1), n, o.shape5)
+    d["H2"] = assemble(lambda v: o.h(v, m2), n, o.shape5)
+    M = dense_meofa(O, d)
+    assert np.abs(M - M.conj().T).max() < 1e-12
+    assert np.linalg.eigvalsh(0.5 * (M + M.conj().T)).min() > 0.5
+    _, lE1 = np.linalg.slogdet(assemble(lambda v: o.deofa(v, m1), n, o.shape5))
+    _, lE2 = np.linalg.slogdet(assemble(lambda v: o.deofa(v, m2), n, o.shape5))
+    sM, lM = np.linalg.slogdet(M)
+    assert abs((lE1 - lE2) + lM) < 1e-9
+    assert abs(sM - 1) < 1e-9
+    eta = I.heatbath_noise(dims, 8)
+    out, _ = A.meofa(o.a, o.U, m1, m2, eta)
+    assert rel(out.reshape(-1), M @ eta.reshape(-1)) < 1e-10
+
+
 def test_heatbath_woodbury_identity(oracle_mod, dense24):
     """Eq. (eofa_heatbath) is the Woodbury rewrite of
     alpha_0 + sum_l alpha_l (M_EOFA + beta_l)^-1: the two agree for any
