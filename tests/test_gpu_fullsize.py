@@ -73,3 +73,47 @@ def test_fullsize_apply_and_solve(env, case):
         r = bs - o.k_sites(psip_h, sites)
         assert np.linalg.norm(r) / np.linalg.norm(bs) < 1e-9, inner
     s.close()
+
+
+def test_fullsize_force_and_heatbath_properties(env):
+    """At 16^3x32 Ls=16 the force must be the derivative of the library's own
+    action S = phi^dag M_EOFA phi: central differences along
+    U_mu(x) -> exp(s T^a) U_mu(x) on the link and generator with the largest
+    force component; and a heatbath with Zolotarev coefficients on an
+    interval holding the spectrum gives epsilon <= 1e-9 (Eq. heatbath_rel_err),
+    properties that hold at any size."""
+    from scipy.linalg import expm
+    from oracle.force import generators
+    from paper_1706_05843_gb300 import heatbath as H
+    from paper_1706_05843_gb300 import rational
+    torch, B, O = env
+    dims, Ls, eps = (16, 16, 16, 32), 16, 0.5
+    U = I.gauge_field(dims, eps, 1)
+    phi = torch.from_numpy(I.heatbath_noise(dims, 31)).cuda()
+    m1, m2 = ACT["m1"], ACT["m2"]
+    s = B.Solver(U, dims, Ls, **ACT)
+    f, _ = s.force(phi, m1, m2, tol=1e-13, inner="f32")
+    f = f.cpu().numpy()
+    Tg = generators()
+    comp = -2.0 * np.einsum("aij,...ji->...a", Tg, f).real    # d^a S per link
+    idx = np.unravel_index(np.argmax(np.abs(comp)), comp.shape)
+    t, z, y, x, mu, gen = (int(i) for i in idx)
+    h = 1e-3
+    vals = []
+    for sg in (+1, -1):
+        Up = U.copy()
+        Up[t, z, y, x, mu] = expm(sg * h * Tg[gen]) @ U[t, z, y, x, mu]
+        sp = B.Solver(Up, dims, Ls, **ACT)
+        m, _ = sp.apply_meofa(phi, m1, m2, tol=1e-13, inner="f32")
+        vals.append(float(torch.vdot(phi.flatten(), m.flatten()).real))
+        sp.close()
+    fd = (vals[0] - vals[1]) / (2 * h)
+    an = comp[idx]
+    assert abs(fd - an) < 2e-3 * abs(an), (fd, an, idx)
+    # heatbath error on [0.5, 30] (the spectrum ends near 21.8 here)
+    r = rational.poles_for(1e-11, 0.5, 30.0)
+    eta = phi
+    out, st = s.heatbath(eta, m1, m2, r, forecast=4, tol=1e-11, inner="f32")
+    mo, _ = s.apply_meofa(out, m1, m2, tol=1e-12, inner="f32")
+    assert H.heatbath_error(eta, out, mo) < 1e-9
+    s.close()
