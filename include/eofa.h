@@ -347,7 +347,10 @@ eofa_status eofa_set_preconditioner(eofa_ctx *ctx, const float *weights);
  * device, with that device current); make that first call before any
  * stream capture.  The call checks that the links are SU(3) (EOFA_ERR_ARG
  * otherwise), which reads a flag back, so it returns after its work on
- * `stream` has finished.  Every call shares the one array and it keeps the
+ * `stream` has finished; for the same reason it cannot be recorded into a
+ * CUDA graph, and on a stream that is being captured it returns
+ * EOFA_ERR_UNSUPPORTED without touching the capture.  Every call shares
+ * the one array and it keeps the
  * last call's contents: calls that overlap on the GPU (other streams, other
  * host threads) race and must not be issued. */
 eofa_status eofa_apply_noalloc(const eofa_params *p, const void *gauge, const void *in,

@@ -8,9 +8,15 @@
 // the default variant only.
 #pragma once
 
+#include <atomic>
+#include <mutex>
+
 #include "dslash.cuh"
 
 namespace eofa {
+
+// devices a process may use the hop kernels on
+constexpr int kHopMaxDevices = 64;
 
 template <typename S, int LS, int K, int VAR>
 static cudaError_t launch_one(const HopArgs& a, const SCoef<typename Traits<S>::R>& c,
@@ -20,37 +26,47 @@ static cudaError_t launch_one(const HopArgs& a, const SCoef<typename Traits<S>::
     const size_t smem = hop_smem_bytes<S, LS, K, VAR>();
     static_assert(hop_smem_bytes<S, LS, K, VAR>() <= 232448, "tile exceeds the 227 KB of shared memory per CTA");
     constexpr bool RCAP = (VAR & 2) != 0;
-    // per instantiation, before its first launch: the shared-memory limit
-    // and the number of CTAs one SM holds (the persistent grid is that many
-    // per SM)
-    static int resident = 0;
+    // per instantiation and device, before its first launch there: the
+    // shared-memory limit (an attribute of the current device) and the
+    // number of CTAs one SM holds (the persistent grid is that many per SM)
+    static std::atomic<int> resident_of[kHopMaxDevices];
+    static std::mutex setup_mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kHopMaxDevices) return cudaErrorInvalidDevice;
+    int resident = resident_of[dev].load(std::memory_order_acquire);
     if (resident == 0) {
-        // the one-time set-up must not run inside a stream capture (the
-        // drivers launch every kernel once before they capture it)
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
-            return cudaErrorStreamCaptureUnsupported;
-        cudaError_t e;
-        if constexpr (RCAP) {
-            e = cudaFuncSetAttribute(hop_kernel_rc<S, LS, K, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
-            if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, hop_kernel_rc<S, LS, K, VAR>, NT,
-                                                                  smem);
-        } else {
-            e = cudaFuncSetAttribute(hop_kernel<S, LS, K, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
-            if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, hop_kernel<S, LS, K, VAR>, NT, smem);
+        std::lock_guard<std::mutex> lock(setup_mu);
+        resident = resident_of[dev].load(std::memory_order_relaxed);
+        if (resident == 0) {
+            // the one-time set-up must not run inside a stream capture (the
+            // drivers launch every kernel once before they capture it)
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+                return cudaErrorStreamCaptureUnsupported;
+            if constexpr (RCAP) {
+                e = cudaFuncSetAttribute(hop_kernel_rc<S, LS, K, VAR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e == cudaSuccess)
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, hop_kernel_rc<S, LS, K, VAR>,
+                                                                      NT, smem);
+            } else {
+                e = cudaFuncSetAttribute(hop_kernel<S, LS, K, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+                if (e == cudaSuccess)
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, hop_kernel<S, LS, K, VAR>, NT,
+                                                                      smem);
+            }
+            if (e != cudaSuccess) return e;
+            if (resident < 1) resident = 1;
+            resident_of[dev].store(resident, std::memory_order_release);
         }
-        if (e != cudaSuccess) return e;
-        if (resident < 1) resident = 1;
     }
     const long nblk = ((long)a.g.Vh + NS - 1) / NS;
     if (nblk == 0) return cudaSuccess;
-    int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<long>(nblk, (long)resident * sms);
     if constexpr (RCAP) hop_kernel_rc<S, LS, K, VAR><<<grid, NT, smem, st>>>(a, c);

@@ -1847,9 +1847,14 @@ extern "C" eofa_status eofa_apply_noalloc(const eofa_params* p, const void* gaug
     const char* why = "";
     eofa_status s = coef_from_params(*p, k, &why);
     if (s != EOFA_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the call reads the SU(3) flag back and waits for it, which a stream
+    // capture cannot hold: refuse instead of invalidating the caller's capture
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return EOFA_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return EOFA_ERR_UNSUPPORTED;
     unsigned char* base = nullptr;
     if ((s = noalloc_scratch(&base)) != EOFA_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
 
     Geom g;
     g.X = p->dims[0]; g.Y = p->dims[1]; g.Z = p->dims[2]; g.T = p->dims[3];

@@ -57,6 +57,21 @@ def test_status_strings(libeofa):
     assert "converged" in B.eofa_status_string(4)
 
 
+def test_status_strings_cover_every_code(libeofa):
+    """Every code of the eofa_status enum in include/eofa.h has its own
+    description; a value outside the enum gets the fallback."""
+    from paper_1706_05843_gb300 import binding as B
+    src = open(HEADER).read()
+    enum = src[src.index("typedef enum"):src.index("} eofa_status;")]
+    codes = [int(v) for v in re.findall(r"EOFA_[A-Z_]+\s*=\s*(\d+)", enum)]
+    assert codes == list(range(len(codes))) and len(codes) == len(B.STATUS)
+    texts = [B.eofa_status_string(c) for c in codes]
+    assert len(set(texts)) == len(codes)
+    fallback = B.eofa_status_string(len(codes))
+    assert fallback not in texts
+    assert B.eofa_status_string(-1) == fallback
+
+
 def test_argument_errors_without_gpu(libeofa):
     """Invalid arguments are rejected before any device work."""
     from paper_1706_05843_gb300 import binding as B
