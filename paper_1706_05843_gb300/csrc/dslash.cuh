@@ -98,12 +98,13 @@ __device__ __forceinline__ C2<R> cmulc(C2<R> a, C2<R> b) {  // conj(a) * b
 }
 
 // ---------------------------------------------------------------------------
-// one hopping direction: acc += phase (1 + SG gamma_MU) W chi, W = U or U^dag
-// u: 18 reals, rows 0..2 of the link (row 2 rebuilt).
+// one hopping direction: acc += (1 + SG gamma_MU) W chi, W = U or U^dag
+// u: 18 reals, rows 0..2 of the link (row 2 rebuilt; the boundary sign of the
+// hop folded in).
 // ---------------------------------------------------------------------------
 template <typename R, int MU, int SG, bool ADJ>
 __device__ __forceinline__ void hop_dir(R* __restrict__ acc, const R* __restrict__ p,
-                                        const R* __restrict__ u, R phase) {
+                                        const R* __restrict__ u) {
     // spin projection: h = psi_up + SG B psi_dn, B = -i sigma_k (k = 1..3) or 1
     R h[12];
     constexpr R s = (R)SG;
@@ -155,8 +156,8 @@ __device__ __forceinline__ void hop_dir(R* __restrict__ acc, const R* __restrict
                     im = fma(-ui, hr, im);
                 }
             }
-            w[sp * 6 + 2 * a] = re * phase;
-            w[sp * 6 + 2 * a + 1] = im * phase;
+            w[sp * 6 + 2 * a] = re;
+            w[sp * 6 + 2 * a + 1] = im;
         }
     }
     // reconstruct: upper += w, lower += SG B^dag w
@@ -389,6 +390,18 @@ __device__ __forceinline__ void ld_half(const R* p, R* v) {
     }
 }
 
+// Column access of a shared tile: one complex per row, rows ST reals apart.
+template <typename R, int LS, int ST>
+__device__ __forceinline__ void col_load(const R* p, C2<R>* v) {
+#pragma unroll
+    for (int k = 0; k < LS; ++k) v[k] = ld_pair(p + k * ST);
+}
+template <typename R, int LS, int ST>
+__device__ __forceinline__ void col_store(R* p, const C2<R>* v) {
+#pragma unroll
+    for (int k = 0; k < LS; ++k) st_pair(p + k * ST, v[k]);
+}
+
 // The fifth-dimension program of one (site, spin, colour) column, in the
 // mirrored coordinate.  hcol: the hop result (overwritten with the output),
 // ycol: the local input; consecutive slices are ST reals apart.
@@ -402,8 +415,7 @@ __device__ __forceinline__ void column_program(R* hcol, const R* ycol, const SCo
         // column, or its transpose for the adjoint kinds
         constexpr bool TR = KT::DAG;
         constexpr bool EO = (KIND == KIND_D_EO || KIND == KIND_D_EO_DAG);
-#pragma unroll
-        for (int k = 0; k < LS; ++k) v[k] = ld_pair((EO ? hcol : ycol) + k * ST);
+        col_load<R, LS, ST>(EO ? hcol : ycol, v);
         C2<R> w[LS];
 #pragma unroll
         for (int k = 0; k < LS; ++k) {
@@ -420,36 +432,31 @@ __device__ __forceinline__ void column_program(R* hcol, const R* ycol, const SCo
 #pragma unroll
             for (int k = 0; k < LS; ++k) v[k] = {(R)(-0.5) * w[k].re, (R)(-0.5) * w[k].im};
         } else {
+            C2<R> h[LS];
+            col_load<R, LS, ST>(hcol, h);
 #pragma unroll
-            for (int k = 0; k < LS; ++k) {
-                const C2<R> h = ld_pair(hcol + k * ST);
-                v[k] = {w[k].re + (R)0.5 * h.re, w[k].im + (R)0.5 * h.im};
-            }
+            for (int k = 0; k < LS; ++k) v[k] = {w[k].re + (R)0.5 * h[k].re, w[k].im + (R)0.5 * h[k].im};
         }
     } else if constexpr (KIND == KIND_EO_MINV) {
-#pragma unroll
-        for (int k = 0; k < LS; ++k) v[k] = ld_pair(hcol + k * ST);
+        col_load<R, LS, ST>(hcol, v);
         op_Minv<R, LS>(v, cf, shv);
         op_fwd<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
         const R f = (R)(-0.5) * hb;
 #pragma unroll
         for (int k = 0; k < LS; ++k) { v[k].re *= f; v[k].im *= f; }
     } else if constexpr (KIND == KIND_EO_MINV_DAG) {
-#pragma unroll
-        for (int k = 0; k < LS; ++k) v[k] = ld_pair(hcol + k * ST);
+        col_load<R, LS, ST>(hcol, v);
         op_fwdT<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
         op_MinvT<R, LS>(v, cf, shv);
 #pragma unroll
         for (int k = 0; k < LS; ++k) { v[k].re *= (R)-0.5; v[k].im *= (R)-0.5; }
     } else {
-#pragma unroll
-        for (int k = 0; k < LS; ++k) v[k] = ld_pair(ycol + k * ST);
+        col_load<R, LS, ST>(ycol, v);
         if constexpr (KIND == KIND_OE_SCHUR || KIND == KIND_FULL) op_M<R, LS>(v, cf, shv);
         if constexpr (KIND == KIND_OE_SCHUR_DAG || KIND == KIND_FULL_DAG) op_MT<R, LS>(v, cf, shv);
         if constexpr (KT::HOP) {
             C2<R> w[LS];
-#pragma unroll
-            for (int k = 0; k < LS; ++k) w[k] = ld_pair(hcol + k * ST);
+            col_load<R, LS, ST>(hcol, w);
             if constexpr (KIND == KIND_OE_SCHUR_DAG || KIND == KIND_FULL_DAG)
                 op_fwdT<R, LS>(w, cf.b5, cf.c5, cf.m * cf.c5);
             const R f = ((KIND == KIND_FULL || KIND == KIND_FULL_DAG) ? (R)-0.5 : (R)0.5) * hb;
@@ -467,8 +474,7 @@ __device__ __forceinline__ void column_program(R* hcol, const R* ycol, const SCo
         if constexpr (KIND == KIND_LOC_DT) op_fwd<R, LS>(v, cf.b5, cf.c5, cf.m * cf.c5);
         if constexpr (KIND == KIND_LOC_DTINV) op_inv<R, LS>(v, cf.ib, cf.zb, cf.mzb, cf.wb);
     }
-#pragma unroll
-    for (int k = 0; k < LS; ++k) st_pair(hcol + k * ST, v[k]);
+    col_store<R, LS, ST>(hcol, v);
 }
 
 // v <- M v for the 5D site (xcb, s) of field y, v = y(xcb, s) on entry: the
@@ -577,6 +583,42 @@ __device__ __forceinline__ void site_MT_dtT(int s, const SCoef<R>& cf, const R* 
 template <typename R> struct LinkStride;
 template <> struct LinkStride<float> { static constexpr int V = 20; };
 template <> struct LinkStride<double> { static constexpr int V = 18; };
+
+// a staged link as 16-byte shared-memory accesses (18 reals; the float
+// stride of 20 keeps every link 16-byte aligned)
+template <typename R>
+__device__ __forceinline__ void ld_link(const R* __restrict__ src, R* u) {
+    if constexpr (sizeof(R) == 4) {
+        const float4* q = reinterpret_cast<const float4*>(src);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 t = q[i];
+            u[4 * i] = t.x; u[4 * i + 1] = t.y; u[4 * i + 2] = t.z; u[4 * i + 3] = t.w;
+        }
+        const float2 t = reinterpret_cast<const float2*>(src)[8];
+        u[16] = t.x; u[17] = t.y;
+    } else {
+        const double2* q = reinterpret_cast<const double2*>(src);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double2 t = q[i];
+            u[2 * i] = t.x; u[2 * i + 1] = t.y;
+        }
+    }
+}
+template <typename R>
+__device__ __forceinline__ void st_link(R* __restrict__ dst, const R* u) {
+    if constexpr (sizeof(R) == 4) {
+        float4* q = reinterpret_cast<float4*>(dst);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) q[i] = make_float4(u[4 * i], u[4 * i + 1], u[4 * i + 2], u[4 * i + 3]);
+        reinterpret_cast<float2*>(dst)[8] = make_float2(u[16], u[17]);
+    } else {
+        double2* q = reinterpret_cast<double2*>(dst);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) q[i] = make_double2(u[2 * i], u[2 * i + 1]);
+    }
+}
 
 // CTA tile: NS 4D sites x Ls slices, one thread per 5D site.  Bit 0 of the
 // variant picks the shape: 0 the default, 1 twice the sites (half for
@@ -756,14 +798,12 @@ __device__ __forceinline__ void hop_body(const HopArgs& a, const SCoef<typename 
                 else link_from_raw<S, R>(reinterpret_cast<const unsigned char*>(dl), u);
                 rebuild_row2(u);
                 // the factor -1 of an antiperiodic or G-parity boundary hop
-                // in x, y, z rides on the staged link (t: applied in the hop);
-                // the branch is uniform over the grid
-                if ((g.gpmask | (g.apmask & 7)) && (j & 3) != 3 && (snb[b * NL + j] >> 31)) {
+                // rides on the staged link; the branch is uniform over the grid
+                if ((g.gpmask | g.apmask) && (snb[b * NL + j] >> 31)) {
 #pragma unroll
                     for (int i = 0; i < 18; ++i) u[i] = -u[i];
                 }
-#pragma unroll
-                for (int i = 0; i < 18; ++i) dl[i] = u[i];
+                st_link(dl, u);
             }
         }
     };
@@ -801,47 +841,40 @@ __device__ __forceinline__ void hop_body(const HopArgs& a, const SCoef<typename 
         if (valid) {
             if constexpr (KT::HOP) {
                 constexpr int FS = KT::DAG ? +1 : -1;  // forward projector 1 + FS gamma
+                // hop k = 2 mu + dir (dir 0 forward, 1 backward)
 #pragma unroll
-                for (int mu = 0; mu < 4; ++mu) {
+                for (int k = 0; k < 8; ++k) {
+                    const int mu = k >> 1, dir = k & 1;
+                    const long ncb = (long)(snc[il * 8 + dir * 4 + mu] & 0x7fffffffu);
+                    R p[24];
+                    load_sp<S, R>(a.in, a.in_nrm, ncb, s, LS, p);
+                    if constexpr (KT::PRE) {
+                        // chi = psi + (c5/b5) L psi (the b5 factor is applied in phase 2)
+                        R q[12];
+                        const int sm = (s == 0) ? LS - 1 : s - 1;
+                        const R fu = (s == 0) ? -cf.mzb : cf.zb;
+                        load_half<S, R>(a.in, a.in_nrm, ncb, sm, LS, 0, q);
 #pragma unroll
-                    for (int dir = 0; dir < 2; ++dir) {
-                        const unsigned nb = snc[il * 8 + dir * 4 + mu];
-                        const long ncb = (long)(nb & 0x7fffffffu);
-                        // the t boundary's sign; x, y, z signs ride on the staged links
-                        const R ph = (mu == 3 && (nb >> 31)) ? (R)-1 : (R)1;
-                        R p[24];
-                        load_sp<S, R>(a.in, a.in_nrm, ncb, s, LS, p);
-                        if constexpr (KT::PRE) {
-                            // chi = psi + (c5/b5) L psi (the b5 factor is applied in phase 2)
-                            R q[12];
-                            const int sm = (s == 0) ? LS - 1 : s - 1;
-                            const R fu = (s == 0) ? -cf.mzb : cf.zb;
-                            load_half<S, R>(a.in, a.in_nrm, ncb, sm, LS, 0, q);
+                        for (int i = 0; i < 12; ++i) p[i] += fu * q[i];
+                        const int sp = (s == LS - 1) ? 0 : s + 1;
+                        const R fd = (s == LS - 1) ? -cf.mzb : cf.zb;
+                        load_half<S, R>(a.in, a.in_nrm, ncb, sp, LS, 1, q);
 #pragma unroll
-                            for (int i = 0; i < 12; ++i) p[i] += fu * q[i];
-                            const int sp = (s == LS - 1) ? 0 : s + 1;
-                            const R fd = (s == LS - 1) ? -cf.mzb : cf.zb;
-                            load_half<S, R>(a.in, a.in_nrm, ncb, sp, LS, 1, q);
-#pragma unroll
-                            for (int i = 0; i < 12; ++i) p[12 + i] += fd * q[i];
-                        }
-                        R u[18];
-                        {
-                            const R* src = slc + (il * 8 + dir * 4 + mu) * LK;
-#pragma unroll
-                            for (int i = 0; i < 18; ++i) u[i] = src[i];
-                        }
-                        if (dir == 0) {
-                            if (mu == 0) hop_dir<R, 0, FS, false>(acc, p, u, ph);
-                            if (mu == 1) hop_dir<R, 1, FS, false>(acc, p, u, ph);
-                            if (mu == 2) hop_dir<R, 2, FS, false>(acc, p, u, ph);
-                            if (mu == 3) hop_dir<R, 3, FS, false>(acc, p, u, ph);
-                        } else {
-                            if (mu == 0) hop_dir<R, 0, -FS, true>(acc, p, u, ph);
-                            if (mu == 1) hop_dir<R, 1, -FS, true>(acc, p, u, ph);
-                            if (mu == 2) hop_dir<R, 2, -FS, true>(acc, p, u, ph);
-                            if (mu == 3) hop_dir<R, 3, -FS, true>(acc, p, u, ph);
-                        }
+                        for (int i = 0; i < 12; ++i) p[12 + i] += fd * q[i];
+                    }
+                    R u[18];
+                    ld_link(slc + (il * 8 + dir * 4 + mu) * LK, u);
+                    // every boundary sign rides on the staged link
+                    if (dir == 0) {
+                        if (mu == 0) hop_dir<R, 0, FS, false>(acc, p, u);
+                        if (mu == 1) hop_dir<R, 1, FS, false>(acc, p, u);
+                        if (mu == 2) hop_dir<R, 2, FS, false>(acc, p, u);
+                        if (mu == 3) hop_dir<R, 3, FS, false>(acc, p, u);
+                    } else {
+                        if (mu == 0) hop_dir<R, 0, -FS, true>(acc, p, u);
+                        if (mu == 1) hop_dir<R, 1, -FS, true>(acc, p, u);
+                        if (mu == 2) hop_dir<R, 2, -FS, true>(acc, p, u);
+                        if (mu == 3) hop_dir<R, 3, -FS, true>(acc, p, u);
                     }
                 }
                 if constexpr (KT::PTW) {
