@@ -185,6 +185,25 @@ def oracle_sample(iters_per_sample):
     return oracle_time(o, phi, iters_per_sample), n_iter, cores
 
 
+FLOPS_PER_SITE = 1520
+
+
+def event_times(torch, stream, reps, fn):
+    """Seconds of `reps` calls of fn, each bracketed by CUDA events on the
+    solve stream; returns (times, last result)."""
+    out = None
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return times, out
+
+
 def _timed(torch, fn):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -436,62 +455,66 @@ def run_ours(args):
     launches = int(statistics.median([s["kernel_launches"] for s in stats]))
     tiles = [B.lib().eofa_tile_variant(solver.ctx, B.PREC[args.inner], k) for k in range(4)]
 
-    # end to end through the public API: pinned host rhs -> device, solve, -> host
+    # end to end through the public API: eofa_solve_host takes the pinned
+    # host right-hand side and returns the solution in host memory; the two
+    # copies run inside the call, on the timed stream
     host_rhs = torch.from_numpy(phi).pin_memory()
     host_sol = torch.empty_like(host_rhs).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
+    solver.solve_host(host_rhs, host_sol, stream=stream, **opts)  # allocates the context's host-solve fields
     barrier()
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(e2e_steps):
-        d_rhs = host_rhs.to(dev, non_blocking=True)
-        out, _ = solver.solve(d_rhs, **opts)
-        host_sol.copy_(out, non_blocking=True)
+        solver.solve_host(host_rhs, host_sol, stream=stream, **opts)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     e2e_val = whole_job_value(max_over_ranks(e0.elapsed_time(e1) / 1e3, ws, dev), e2e_steps, ws)
 
-    # the other precisions once each, outside the timed region
+    # the other precisions outside the timed region: repeated solves timed
+    # with CUDA events on the solve stream, median and spread
     extra = {}
     if rank == 0 and not args.quick:
         for inner in ["f64", "f32", "f16", "bf16"]:
             if inner == args.inner:
                 continue
             solver.solve(rhs, out=sol, tol=TOL, inner=inner, check=False)  # tunes and captures this precision
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            _, st = solver.solve(rhs, out=sol, tol=TOL, inner=inner, check=False)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            extra[inner] = {"s_per_solve": dt, "true_res": st.true_res, "outer": st.outer_iters,
+            reps = args.cmp_reps
+            times, st = event_times(torch, stream, reps,
+                                    lambda: solver.solve(rhs, out=sol, tol=TOL, inner=inner, check=False)[1])
+            extra[inner] = {"s_per_solve": statistics.median(times), "s_min": min(times), "s_max": max(times),
+                            "repeats": reps, "true_res": st.true_res, "outer": st.outer_iters,
                             "inner_iters": st.inner_iters, "status": st.status,
-                            "hop_GBps": st.hop_bytes / (st.hop_ms * 1e-3) / 1e9 if st.hop_ms else None}
+                            "hop_GBps": st.hop_bytes / (st.hop_ms * 1e-3) / 1e9 if st.hop_ms else None,
+                            "hop_ms_per_launch": st.hop_ms / st.hop_launches if st.hop_launches else None}
 
     workloads = {}
     if rank == 0 and not args.quick:
         # the paper's comparison (Sec. V.B): even-odd on the unpreconditioned
         # system with the dense Ls x Ls site block, same outer loop and inner precision
         solver.solve(rhs, out=sol, tol=TOL, inner=args.inner, method=1, check=False)  # set-up and capture
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, st = solver.solve(rhs, out=sol, tol=TOL, inner=args.inner, method=1, check=False)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+        reps = max(5, args.cmp_reps)
+        times, st = event_times(torch, stream, reps,
+                                lambda: solver.solve(rhs, out=sol, tol=TOL, inner=args.inner, method=1,
+                                                     check=False)[1])
+        dt = statistics.median(times)
+        cay = [s_["seconds"] for s_ in stats]
         workloads["dense_vs_cayley"] = {
             "inner": args.inner,
-            "dense": {"s_per_solve": dt, "inner_iters": st.inner_iters, "outer": st.outer_iters,
+            "dense": {"s_per_solve": dt, "s_min": min(times), "s_max": max(times), "repeats": reps,
+                      "inner_iters": st.inner_iters, "outer": st.outer_iters,
                       "true_res": st.true_res, "status": st.status,
                       "hop_GBps": st.hop_bytes / (st.hop_ms * 1e-3) / 1e9 if st.hop_ms else None},
-            "cayley": {"s_per_solve": value, "inner_iters": stats[-1]["inner_iters"],
-                       "outer": stats[-1]["outer_iters"]},
+            "cayley": {"s_per_solve": value, "repeats": args.steps, "host_s_min": min(cay), "host_s_max": max(cay),
+                       "inner_iters": stats[-1]["inner_iters"], "outer": stats[-1]["outer_iters"]},
             "cayley_speedup": dt / value if value else None}
         workloads["heatbath"] = run_heatbath(B, I, torch, dev, solver)
         solver.close()
         workloads["gparity_xyz"] = run_gparity(B, I, torch, dev)
         workloads["batched_16rhs_uneven"] = run_batched(B, I, torch, dev)
         workloads["24^3x64_Ls12_4rhs"] = run_multi_rhs(B, I, torch, dev)
-        if args.learned:
+        if not args.no_learned:
             workloads["learned_32^3x64_Ls12"] = run_learned(B, I, torch, dev)
 
     if rank != 0:
@@ -521,6 +544,19 @@ def run_ours(args):
                              f"workload, {pi:.3f} s/iteration, scaled by the oracle's recorded {n_iter} "
                              f"iterations to r=1e-10"}
     f64 = extra.get("f64", {}).get("s_per_solve")
+    # the FP64 hop (the plain FP64 CG comparator) against the measured FP64
+    # FMA throughput: SURVEY-style count of 1520 flops per 5D output site per
+    # launch (1320 Wilson hop, 50 for b5 + c5 L, 150 for the s-space inverse)
+    roofline_f64 = None
+    if rank == 0 and not args.quick and extra.get("f64", {}).get("hop_ms_per_launch"):
+        pk64 = B.eofa_measure_fma("f64", reps=5, stream=stream)
+        pk32 = B.eofa_measure_fma("f32", reps=5, stream=stream)
+        n5 = int(np.prod(w["dims"])) // 2 * w["Ls"]
+        tf = FLOPS_PER_SITE * n5 / (extra["f64"]["hop_ms_per_launch"] * 1e-3) / 1e12
+        roofline_f64 = {"bound": "alu", "kernel": "hop_kernel<double, Ls=16> (4 kinds)", "achieved": tf,
+                        "peak": pk64, "unit": "TFLOP/s", "frac": tf / pk64, "flops_per_site": FLOPS_PER_SITE,
+                        "peak_kind": "measured here: eofa_measure_fma FP64 (independent FMA chains, CUDA events)",
+                        "fp32_fma_peak_tflops": pk32}
     line = {
         "metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
@@ -535,7 +571,9 @@ def run_ours(args):
         "solve": {"true_res": main["true_res"], "outer_iters": main["outer_iters"],
                   "inner_iters": main["inner_iters"], "kernel_launches_per_solve": launches},
         "other_precisions": extra,
+        "roofline_f64": roofline_f64,
         "speedup_vs_fp64": (f64 / value) if f64 and ws == 1 else None,
+        "speedup_vs_fp64_repeats": extra.get("f64", {}).get("repeats"),
         "other_workloads": workloads,
     }
     print(json.dumps(line))
@@ -553,8 +591,10 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=4, help="oracle iterations per CPU sample")
     ap.add_argument("--quick", action="store_true", help="skip the other-precision solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--learned", action="store_true",
-                    help="also train the learned preconditioner and time it at 32^3x64 Ls=12 (minutes)")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip training the learned preconditioner and timing it at 32^3x64 Ls=12")
+    ap.add_argument("--cmp-reps", type=int, default=5,
+                    help="repeats of each comparison solve (other precisions, dense scheme)")
     ap.add_argument("--profile", action="store_true",
                     help="one solve capped at 16 inner iterations, nothing else (for ncu captures)")
     ap.add_argument("--host-loop", action="store_true",
@@ -562,7 +602,7 @@ def main():
                          "ncu does not profile the kernels inside the solver's conditional graph nodes)")
     args = ap.parse_args()
     if args.profile:
-        args.quick, args.no_cpu, args.steps, args.warmup = True, True, 1, 0
+        args.quick, args.no_cpu, args.steps, args.warmup, args.no_learned = True, True, 1, 0, True
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -175,6 +175,21 @@ eofa_status eofa_solve(eofa_ctx *ctx, const void *rhs, void *sol,
                        const eofa_solve_opts *opts, eofa_solve_stats *stats,
                        void *stream);
 
+/* eofa_solve with the right-hand side and the solution in HOST memory
+ * (complex128, same layout): the call copies rhs to the device, solves, and
+ * copies the solution back, all on `stream`, and returns when the solution
+ * is in `sol`.  The device copies live in two 5D work fields that the
+ * context allocates on first use and keeps (the same ones the action calls
+ * use).  Page-locked host buffers give the full copy bandwidth; pageable ones
+ * work too.  With opts->use_guess, sol holds the initial guess on entry.  The
+ * solution is copied back for every status the solver itself returns
+ * (EOFA_OK, EOFA_ERR_NOT_CONVERGED, EOFA_ERR_TIMEOUT, EOFA_ERR_NONFINITE);
+ * argument and CUDA errors leave sol untouched.  End-to-end entry of the
+ * solve as Sec. V.A describes it (the paper has no separate host form). */
+eofa_status eofa_solve_host(eofa_ctx *ctx, const double *rhs, double *sol,
+                            const eofa_solve_opts *opts, eofa_solve_stats *stats,
+                            void *stream);
+
 /* ---------------------------------------------------------------------------
  * EOFA action and heatbath (Sec. III.A Eq. eofa_action, Sec. III.B
  * Eq. eofa_heatbath, App. A).  These reuse the context's lattice and gauge
@@ -355,6 +370,15 @@ eofa_status eofa_set_preconditioner(eofa_ctx *ctx, const float *weights);
  * host threads) race and must not be issued. */
 eofa_status eofa_apply_noalloc(const eofa_params *p, const void *gauge, const void *in,
                                void *out, void *stream);
+
+/* Measured throughput of the device's fused multiply-add pipe, a
+ * measurement utility with no counterpart in the paper: prec EOFA_F64 or
+ * EOFA_F32; a kernel of independent FMA chains (one CTA set per SM of the
+ * current device) is timed with CUDA events on `stream` after a warm-up,
+ * and *tflops receives 2 x FMAs / seconds / 1e12 (the best of `reps`
+ * launches, reps >= 1).  Synchronises the stream.  EOFA_ERR_ARG for a bad
+ * prec, reps or NULL tflops. */
+eofa_status eofa_measure_fma(int prec, int reps, double *tflops, void *stream);
 
 /* Static description of a status code. */
 const char *eofa_status_string(eofa_status s);

@@ -84,6 +84,8 @@ SIGNATURES = {
     "eofa_apply_batched": ([C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp), C.c_int, _vp], C.c_int),
     "eofa_solve_batched": ([C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp),
                             C.POINTER(eofa_solve_opts), C.POINTER(eofa_solve_stats), _vp], C.c_int),
+    "eofa_solve_host": ([_vp, _dp, _dp, C.POINTER(eofa_solve_opts), C.POINTER(eofa_solve_stats), _vp], C.c_int),
+    "eofa_measure_fma": ([C.c_int, C.c_int, _dp, _vp], C.c_int),
     "eofa_destroy": ([_vp], None),
     "eofa_apply_noalloc": ([C.POINTER(eofa_params), _vp, _vp, _vp, _vp], C.c_int),
     "eofa_net_forward": ([_fp, C.POINTER(C.c_int), C.c_int, _vp, _vp, _vp], C.c_int),
@@ -199,6 +201,35 @@ def eofa_solve(ctx, rhs, sol, opts, stream=None, check=True):
     if check:
         _check(ctx, s)
     return st
+
+
+def _hptr(a):
+    """Host complex128 field (numpy array or CPU torch tensor, contiguous)."""
+    if isinstance(a, np.ndarray):
+        if not (a.dtype == np.complex128 and a.flags["C_CONTIGUOUS"]):
+            raise TypeError("host fields must be contiguous complex128 arrays")
+        return a.ctypes.data_as(_dp)
+    import torch
+    if not (isinstance(a, torch.Tensor) and not a.is_cuda and a.dtype == torch.complex128 and a.is_contiguous()):
+        raise TypeError("host fields must be contiguous complex128 CPU tensors or numpy arrays")
+    return C.cast(C.c_void_p(a.data_ptr()), _dp)
+
+
+def eofa_solve_host(ctx, rhs, sol, opts, stream=None, check=True):
+    """eofa_solve with host rhs and sol (copies inside the call)."""
+    st = eofa_solve_stats()
+    s = lib().eofa_solve_host(ctx, _hptr(rhs), _hptr(sol), C.byref(opts), C.byref(st), _stream(stream))
+    if check:
+        _check(ctx, s)
+    return st
+
+
+def eofa_measure_fma(prec, reps=5, stream=None):
+    """Measured FMA throughput of the current device in TFLOP/s."""
+    out = C.c_double(0.0)
+    _check(None, lib().eofa_measure_fma(PREC[prec] if isinstance(prec, str) else int(prec), int(reps), C.byref(out),
+                                        _stream(stream)))
+    return out.value
 
 
 def eofa_set_system(ctx, m1, m2, m3, beta, pm):
@@ -381,6 +412,11 @@ class Solver:
         sol = self._new() if out is None else out
         st = eofa_solve(self.ctx, rhs, sol, make_opts(**opts), stream, check=check)
         return sol, st
+
+    def solve_host(self, rhs, out, stream=None, check=True, **opts):
+        """Solve with host rhs and host out (numpy complex128 or CPU tensors)."""
+        st = eofa_solve_host(self.ctx, rhs, out, make_opts(**opts), stream, check=check)
+        return out, st
 
     def hop_bytes(self, prec, with_local):
         return eofa_hop_bytes(self.ctx, prec, with_local)

@@ -1627,6 +1627,27 @@ eofa_status eofa_solve(eofa_ctx* ctx, const void* rhs, void* sol, const eofa_sol
     return s;
 }
 
+eofa_status eofa_solve_host(eofa_ctx* ctx, const double* rhs, double* sol, const eofa_solve_opts* opts,
+                            eofa_solve_stats* stats, void* stream) {
+    if (!ctx || !rhs || !sol || !opts || rhs == sol) return EOFA_ERR_ARG;
+    eofa_ctx* c = ctx;
+    c->err.clear();
+    cudaStream_t st = (cudaStream_t)stream;
+    double* drhs = act_buf(c, 0);
+    double* dsol = act_buf(c, 1);
+    if (!drhs || !dsol) return fail(c, EOFA_ERR_OOM, "work fields of the host solve");
+    const size_t bytes = (size_t)c->n5 * 2 * 24 * sizeof(double);
+    CK(cudaMemcpyAsync(drhs, rhs, bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    if (opts->use_guess) CK(cudaMemcpyAsync(dsol, sol, bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    eofa_status s = solve_impl(c, drhs, dsol, *opts, stats, st);
+    if (stats) stats->status = s;
+    if (s == EOFA_OK || s == EOFA_ERR_NOT_CONVERGED || s == EOFA_ERR_TIMEOUT || s == EOFA_ERR_NONFINITE) {
+        CK(cudaMemcpyAsync(sol, dsol, bytes, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+        CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    }
+    return s;
+}
+
 eofa_status eofa_set_system(eofa_ctx* ctx, double m1, double m2, double m3, double beta, int pm) {
     if (!ctx) return EOFA_ERR_ARG;
     ctx->err.clear();

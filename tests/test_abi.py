@@ -92,6 +92,12 @@ def test_argument_errors_without_gpu(libeofa):
         assert libeofa.eofa_create_gparity(C.byref(p), C.c_void_p(1), dirs, None, C.byref(ctx)) == 1
     p = B.make_params((4, 4, 4, 3), 8)
     assert libeofa.eofa_create_gparity(C.byref(p), C.c_void_p(1), 1, None, C.byref(ctx)) == 1
+    # host-buffer solve and the FMA probe: argument checks before any device work
+    assert libeofa.eofa_solve_host(None, None, None, None, None, None) == 1
+    out = C.c_double(0.0)
+    assert libeofa.eofa_measure_fma(2, 3, C.byref(out), None) == 1   # FP16 has no FMA probe
+    assert libeofa.eofa_measure_fma(0, 0, C.byref(out), None) == 1   # reps < 1
+    assert libeofa.eofa_measure_fma(0, 3, None, None) == 1
     # action calls without a context
     opts = B.make_opts(tol=1e-10)
     assert libeofa.eofa_set_system(None, 0.04, 1.0, 0.04, -1.0, 1) == 1

@@ -1,0 +1,70 @@
+"""GPU tests of the host-buffer solve and the FMA throughput probe.
+
+eofa_solve_host copies a host right-hand side in and the solution out inside
+the call; the answer must be the device solve's (the solver is
+deterministic, so bit for bit) and is judged by the oracle.  The FMA probe
+must report a positive throughput with FP32 above FP64.
+"""
+import numpy as np
+import pytest
+
+from paper_1706_05843_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+ACT = dict(M5=1.8, b=1.5, c=0.5, m1=0.04, m2=1.0, m3=0.04, beta=-1.0, pm=1, t_bc=-1)
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1706_05843_gb300 import build
+    build.build()
+    import oracle
+    oracle.build()
+    from paper_1706_05843_gb300 import binding as B
+    B.lib()
+    return torch, B, oracle
+
+
+@pytest.mark.parametrize("inner", ["f64", "f32"])
+def test_solve_host_matches_device_solve(env, inner):
+    torch, B, O = env
+    dims, Ls = (4, 4, 4, 4), 8
+    U = I.gauge_field(dims, 0.3, 1)
+    s = B.Solver(U, dims, Ls, **ACT)
+    o = O.Oracle(O.Action(dims=dims, Ls=Ls, **ACT), U)
+    phi = I.gaussian_fermion(dims, Ls, 1001)
+    dev, st_d = s.solve(torch.from_numpy(phi).cuda(), tol=1e-10, inner=inner)
+    host_rhs = torch.from_numpy(phi).pin_memory()
+    host_sol = torch.empty_like(host_rhs).pin_memory()
+    _, st_h = s.solve_host(host_rhs, host_sol, tol=1e-10, inner=inner)
+    assert st_h.status == 0 and st_h.inner_iters == st_d.inner_iters
+    assert np.array_equal(host_sol.numpy(), dev.cpu().numpy())
+    assert np.linalg.norm(phi - o.hsys(host_sol.numpy())) / np.linalg.norm(phi) <= 1e-10
+    # pageable numpy buffers and the initial guess: restarting from the
+    # converged answer needs no inner iteration
+    out = host_sol.numpy().copy()
+    _, st_g = s.solve_host(phi, out, tol=1e-10, inner=inner, use_guess=True)
+    assert st_g.status == 0 and st_g.inner_iters == 0
+    s.close()
+
+
+def test_solve_host_rejects_device_arguments(env):
+    torch, B, O = env
+    dims, Ls = (4, 4, 4, 4), 8
+    s = B.Solver(I.gauge_field(dims, 0.3, 1), dims, Ls, **ACT)
+    x = torch.zeros((4, 4, 4, 4, Ls, 4, 3), dtype=torch.complex128, device="cuda")
+    with pytest.raises(TypeError):
+        s.solve_host(x, x.cpu())
+    s.close()
+
+
+def test_measure_fma(env):
+    torch, B, O = env
+    f64 = B.eofa_measure_fma("f64", reps=3)
+    f32 = B.eofa_measure_fma("f32", reps=3)
+    print(f"FMA throughput: FP64 {f64:.2f} TFLOP/s, FP32 {f32:.2f} TFLOP/s")
+    assert 0.0 < f64 < f32
