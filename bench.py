@@ -352,6 +352,30 @@ def run_learned(B, I, torch, dev):
     return res
 
 
+def run_fma_peaks(args):
+    """FP64 and FP32 FMA throughput of GPU 0 (eofa_measure_fma, best of 5
+    launches each, repeated for about 4 s) with nvidia-smi clock samples
+    taken meanwhile; prints one JSON line."""
+    import torch
+    from paper_1706_05843_gb300 import binding as B
+    from paper_1706_05843_gb300 import build as BLD
+    torch.cuda.set_device(0)
+    if not os.path.exists(B.LIB_PATH):
+        BLD.build()
+    B.lib()
+    uuid = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
+    sampler = ClockSampler(uuid)
+    time.sleep(0.3)
+    res = {"f64": [], "f32": []}
+    t0 = time.time()
+    while time.time() - t0 < 4.0:
+        for k in res:
+            res[k].append(B.eofa_measure_fma(k, reps=5))
+    clocks = sampler.stop()
+    print(json.dumps({k + "_tflops": {"best": max(v), "median": statistics.median(v), "runs": len(v)}
+                      for k, v in res.items()} | {"clocks": clocks}))
+
+
 def run_reference(args):
     ws, rank, _ = dist_setup()
     if rank != 0:
@@ -600,7 +624,12 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="timed solves with the host-driven CG loop and every hop timed (ncu launch lists: "
                          "ncu does not profile the kernels inside the solver's conditional graph nodes)")
+    ap.add_argument("--fma-peaks", action="store_true",
+                    help="only measure the FP64/FP32 FMA throughput with clock samples and print it")
     args = ap.parse_args()
+    if args.fma_peaks:
+        run_fma_peaks(args)
+        return
     if args.profile:
         args.quick, args.no_cpu, args.steps, args.warmup, args.no_learned = True, True, 1, 0, True
     if args.impl == "reference":
