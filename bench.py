@@ -74,6 +74,15 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def bf16_peaks():
+    """(burst, sustained) dense BF16 TFLOP/s from MEASURED_PEAKS.json, else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"]))
+    return 1900.0, 1700.0
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -318,9 +327,11 @@ def run_gparity(B, I, torch, dev):
 
 def run_learned(B, I, torch, dev):
     """Learned preconditioner: trained on 2000 (residual, error) pairs from
-    16^3x32 Ls=16 solves (gauge seed 3), used in flexible GCR at 32^3x64
-    Ls=12 (FP32 inner, FP64 correction to 1e-10), against plain CGNR and the
-    untrained network."""
+    16^3x32 Ls=16 solves (gauge seed 3; a further 200 pairs held out to
+    measure the trained network's error on unseen pairs), used in flexible
+    GCR at 32^3x64 Ls=12 (FP32 inner, FP64 correction to 1e-10), against
+    plain CGNR and the untrained network; the convolution's tensor-core rate
+    from the forward passes of one application."""
     act = dict(WORKLOAD["action"])
     rng = np.random.default_rng(17)
     w0 = np.concatenate([rng.standard_normal(81 * co * ci) * np.sqrt(2.0 / (81 * ci))
@@ -328,8 +339,8 @@ def run_learned(B, I, torch, dev):
     dims_t, Ls_t = (16, 16, 16, 32), 16
     Ut = torch.from_numpy(I.gauge_field(dims_t, 0.5, 3)).to(dev)
     st_ = B.Solver(Ut, dims_t, Ls_t, **act)
-    srcs = [torch.from_numpy(I.gaussian_fermion(dims_t, Ls_t, 5000 + i)).to(dev) for i in range(40)]
-    opts = B.make_train_opts(pairs=2000, snapshot_every=8, epochs=3, batch=8, lr=1e-3, solve_tol=1e-6)
+    srcs = [torch.from_numpy(I.gaussian_fermion(dims_t, Ls_t, 5000 + i)).to(dev) for i in range(46)]
+    opts = B.make_train_opts(pairs=2000, snapshot_every=8, epochs=3, batch=8, lr=1e-3, solve_tol=1e-6, holdout=200)
     t_train, (w, tst) = _timed(torch, lambda: B.eofa_train_preconditioner(st_.ctx, srcs, w0, opts))
     st_.close()
     del srcs, Ut
@@ -339,7 +350,9 @@ def run_learned(B, I, torch, dev):
     del U
     rhs = torch.from_numpy(I.gaussian_fermion(dims, Ls, 1001)).to(dev)
     sol = torch.empty_like(rhs)
-    res = {"train": dict(tst.as_dict(), wall_s=t_train)}
+    res = {"train": dict(tst.as_dict(), wall_s=t_train,
+                         holdout_gain=(1.0 - tst.holdout_loss_final / tst.holdout_loss_init)
+                         if tst.holdout_loss_init > 0 else None)}
     s.solve(rhs, out=sol, tol=TOL, inner="f32")
     dt, (_, st) = _timed(torch, lambda: s.solve(rhs, out=sol, tol=TOL, inner="f32"))
     res["cgnr"] = {"s": dt, "inner_iters": st.inner_iters, "true_res": st.true_res}
@@ -347,7 +360,16 @@ def run_learned(B, I, torch, dev):
         B.eofa_set_preconditioner(s.ctx, weights)
         dt, (_, st) = _timed(torch, lambda: s.solve(rhs, out=sol, tol=TOL, inner="f32", precond=1))
         res[name] = {"s": dt, "inner_iters": st.inner_iters, "gcr_steps": st.precond_iters,
-                     "fallbacks": st.precond_fallbacks, "true_res": st.true_res}
+                     "fallbacks": st.precond_fallbacks, "true_res": st.true_res,
+                     "net_ms": st.precond_ms, "net_applications": st.precond_iters}
+        if st.precond_iters and st.precond_ms > 0:
+            # executed tensor-core work of one application: 3 layers of 81 taps, 32 x 32 padded
+            # channels, on every site of the full lattice and every slice
+            rows = int(np.prod(dims)) * Ls
+            flops = 2.0 * rows * 3 * 81 * 32 * 32
+            tf = flops * st.precond_iters / (st.precond_ms * 1e-3) / 1e12
+            res[name]["net_tflops"] = tf
+            res[name]["net_frac_of_bf16_sustained"] = tf / bf16_peaks()[1]
     s.close()
     return res
 

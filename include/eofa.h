@@ -126,6 +126,7 @@ typedef struct {
     long kernel_launches;/* kernels this library launched during the call */
     int precond_iters;   /* flexible-GCR steps with the learned preconditioner (precond = 1) */
     int precond_fallbacks; /* inner solves handed to CGNR because a GCR cycle did not halve |r| */
+    double precond_ms;   /* device time of the network applications (precond = 1; CUDA events) */
 } eofa_solve_stats;
 
 typedef struct eofa_ctx eofa_ctx;
@@ -286,7 +287,11 @@ void eofa_destroy(eofa_ctx *ctx);
  * spin-colour components in the order [spin][colour][re, im]); no biases;
  * LeakyReLU with slope 0.1 after the first two layers.  On the device the
  * weights and activations are BF16 and the products accumulate in FP32 on
- * the tensor cores.
+ * the tensor cores (forward and input-gradient products with tcgen05.mma
+ * into tensor memory, weight gradients with mma.sync).  The tcgen05
+ * convolution bounds its waits on the tensor cores; should one expire, the
+ * call returns EOFA_ERR_TIMEOUT (forward, backward, training, and a solve
+ * with the preconditioner) instead of a result.
  *
  * Weights: EOFA_NET_WEIGHTS host floats, the three layers one after another,
  * each as W[tap][co][ci] with (ci, co) = (24, 32), (32, 32), (32, 24) and
@@ -316,6 +321,8 @@ typedef struct {
     int batch;            /* slices per Adam step, at most Ls/2 */
     double lr;            /* Adam step size */
     double solve_tol;     /* relative tolerance of the FP32 solves that make the pairs */
+    int holdout;          /* further pairs, harvested after the training pairs and never
+                             trained on, to measure what training gains (0: none) */
 } eofa_train_opts;
 
 typedef struct {
@@ -323,6 +330,9 @@ typedef struct {
     double loss_first;    /* mean relative squared error of the first step */
     double loss_last;     /* same, last step */
     double seconds;
+    int holdout_pairs;        /* held-out pairs found (<= opts->holdout) */
+    double holdout_loss_init; /* mean relative squared error on them, initial weights */
+    double holdout_loss_final;/* same, trained weights */
 } eofa_train_stats;
 
 /* Train the network on the context's lattice.  For each source (device
@@ -332,7 +342,10 @@ typedef struct {
  * restricted to one s-slice.  Adam on the relative squared error
  * |net(r) - e|^2 / |e|^2 over the odd sites, starting from init_weights
  * (host; the random initial values are the caller's).  The trained weights
- * go to weights_out (host).  Sources must be enough to give `pairs` pairs. */
+ * go to weights_out (host).  Sources must be enough to give `pairs` pairs;
+ * with opts->holdout > 0 the sources' further pairs (up to holdout) are kept
+ * out of training and the loss on them is reported for the initial and the
+ * trained weights. */
 eofa_status eofa_train_preconditioner(eofa_ctx *ctx, const void *const *sources, int n_sources,
                                       const float *init_weights, const eofa_train_opts *opts,
                                       float *weights_out, eofa_train_stats *stats, void *stream);

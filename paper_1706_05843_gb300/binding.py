@@ -48,7 +48,8 @@ class eofa_solve_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("inner_iters", C.c_int),
                 ("hop_launches", C.c_int), ("true_res", C.c_double), ("recur_res", C.c_double),
                 ("seconds", C.c_double), ("hop_ms", C.c_double), ("hop_bytes", C.c_double),
-                ("kernel_launches", C.c_long), ("precond_iters", C.c_int), ("precond_fallbacks", C.c_int)]
+                ("kernel_launches", C.c_long), ("precond_iters", C.c_int), ("precond_fallbacks", C.c_int),
+                ("precond_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -59,12 +60,13 @@ NET_WEIGHTS = 207360
 
 class eofa_train_opts(C.Structure):
     _fields_ = [("pairs", C.c_int), ("snapshot_every", C.c_int), ("epochs", C.c_int), ("batch", C.c_int),
-                ("lr", C.c_double), ("solve_tol", C.c_double)]
+                ("lr", C.c_double), ("solve_tol", C.c_double), ("holdout", C.c_int)]
 
 
 class eofa_train_stats(C.Structure):
     _fields_ = [("pairs", C.c_int), ("steps", C.c_int), ("solves", C.c_int), ("loss_first", C.c_double),
-                ("loss_last", C.c_double), ("seconds", C.c_double)]
+                ("loss_last", C.c_double), ("seconds", C.c_double), ("holdout_pairs", C.c_int),
+                ("holdout_loss_init", C.c_double), ("holdout_loss_final", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -332,10 +334,10 @@ def eofa_net_backward(weights, dims, inp, dout, din=None, stream=None):
     return dw
 
 
-def make_train_opts(pairs=2000, snapshot_every=8, epochs=3, batch=8, lr=1e-3, solve_tol=1e-6):
+def make_train_opts(pairs=2000, snapshot_every=8, epochs=3, batch=8, lr=1e-3, solve_tol=1e-6, holdout=0):
     o = eofa_train_opts()
     o.pairs, o.snapshot_every, o.epochs, o.batch = int(pairs), int(snapshot_every), int(epochs), int(batch)
-    o.lr, o.solve_tol = float(lr), float(solve_tol)
+    o.lr, o.solve_tol, o.holdout = float(lr), float(solve_tol), int(holdout)
     return o
 
 

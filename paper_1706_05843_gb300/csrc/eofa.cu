@@ -66,6 +66,8 @@ struct eofa_ctx {
     std::vector<double> ev_bytes;
     long launches = 0;  // kernels launched since the last reset
     int gcr_steps = 0, gcr_fallbacks = 0;  // learned-preconditioner statistics of the current solve
+    double net_ms = 0.0;                   // device time of the network applications
+    cudaEvent_t nev[2] = {};               // events around one network application
     // autotuned CTA tile variant of the four inner-solver hop kinds, per precision
     bool tuned[4] = {};
     int tile[4][4] = {};
@@ -824,6 +826,7 @@ eofa_status solve_begin(eofa_ctx* c, const double* rhs, const double* sol, const
     c->timing = o.kernel_timing != 0;
     c->launches = 0;
     c->gcr_steps = c->gcr_fallbacks = 0;
+    c->net_ms = 0.0;
     c->hop_ms = 0.0;
     c->hop_launches = 0;
     c->hop_bytes = 0.0;
@@ -943,6 +946,7 @@ eofa_status solve_end(eofa_ctx* c, double* sol, const eofa_solve_opts& o, SolveS
     S.kernel_launches = c->launches;
     S.precond_iters = c->gcr_steps;
     S.precond_fallbacks = c->gcr_fallbacks;
+    S.precond_ms = c->net_ms;
     eofa_status result = ss.result;
     if (result == EOFA_OK && ss.bb != 0.0 && !(S.true_res <= o.tol * 1.0000001))
         result = fail(c, EOFA_ERR_NOT_CONVERGED, "true residual above tol after the outer loop");
@@ -1753,6 +1757,8 @@ void eofa_destroy(eofa_ctx* ctx) {
     if (!ctx) return;
     for (void* p : ctx->allocs) cudaFree(p);
     for (cudaEvent_t e : ctx->evs) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->nev)
+        if (e) cudaEventDestroy(e);
     for (auto& row : ctx->gev)
         for (cudaEvent_t e : row)
             if (e) cudaEventDestroy(e);
@@ -1995,8 +2001,10 @@ extern "C" eofa_status eofa_net_forward(const float* weights, const int dims[4],
     if (e == cudaSuccess) e = net_forward(n, g, a0, a1, a2, o32, st);
     if (e == cudaSuccess) e = unpack_out(o32, (float*)out, rows, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    int fault = 0;
+    if (e == cudaSuccess) e = net_fault(&fault);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? EOFA_ERR_OOM : EOFA_ERR_CUDA;
-    return EOFA_OK;
+    return fault ? EOFA_ERR_TIMEOUT : EOFA_OK;
 }
 
 extern "C" eofa_status eofa_net_backward(const float* weights, const int dims[4], int nslices, const void* in,
@@ -2027,8 +2035,10 @@ extern "C" eofa_status eofa_net_backward(const float* weights, const int dims[4]
     if (e == cudaSuccess && din) e = unpack_out(din32, (float*)din, rows, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dweights, dW, sizeof(float) * kNetWeights, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    int fault = 0;
+    if (e == cudaSuccess) e = net_fault(&fault);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? EOFA_ERR_OOM : EOFA_ERR_CUDA;
-    return EOFA_OK;
+    return fault ? EOFA_ERR_TIMEOUT : EOFA_OK;
 }
 
 // ===========================================================================
@@ -2087,6 +2097,15 @@ ConvGeom conv_geom_of(const eofa_ctx* c, int slices) {
     return cg;
 }
 
+// after a synchronisation: a tensor-core convolution that gave up on a
+// bounded wait left its output unwritten
+eofa_status check_net(eofa_ctx* c) {
+    int f = 0;
+    CK(net_fault(&f), "net_fault");
+    if (f) return fail(c, EOFA_ERR_TIMEOUT, "tensor-core convolution: a bounded wait expired");
+    return EOFA_OK;
+}
+
 // z = net(r) for every s-slice of an odd-parity FP32 field
 eofa_status net_apply(eofa_ctx* c, VecRef in, VecRef out, cudaStream_t st) {
     CKL(embed_odd(in, c->act[0], c->g, -1, 1.0, c->scal, -1, st), "embed");
@@ -2120,6 +2139,8 @@ eofa_status run_fgcr(eofa_ctx* c, double tol, int maxit, int* iters, cudaStream_
     const VecRef none{};
     eofa_status s;
     if ((s = ensure_learned(c))) return s;
+    for (cudaEvent_t& e : c->nev)
+        if (!e) CK(cudaEventCreate(&e), "cudaEventCreate");
     CKL(blas_copy(EOFA_F32, c->gr, EOFA_F32, in.r, n5, Ls, 1.0, -1, red(c, FIN_NONE), st), "copy");
     CKL(blas_zero(EOFA_F32, c->gx, n5, Ls, st), "zero");
     double rr, im;
@@ -2132,7 +2153,9 @@ eofa_status run_fgcr(eofa_ctx* c, double tol, int maxit, int* iters, cudaStream_
     for (;;) {
         const double cycle_rr = rr;
         for (int k = 0; k < kGcrM; ++k) {
+            CK(cudaEventRecord(c->nev[0], st), "cudaEventRecord");
             if ((s = net_apply(c, c->gr, c->gz[k], st))) return s;
+            CK(cudaEventRecord(c->nev[1], st), "cudaEventRecord");
             if ((s = hop(c, EOFA_F32, KIND_EO_MINV, 0, c->gz[k], none, in.t, red(c, FIN_NONE), nullptr, st)))
                 return s;
             if ((s = hop(c, EOFA_F32, KIND_OE_SCHUR, 1, in.t, c->gz[k], c->gw[k], red(c, FIN_NONE), nullptr, st)))
@@ -2144,7 +2167,10 @@ eofa_status run_fgcr(eofa_ctx* c, double tol, int maxit, int* iters, cudaStream_
                 CKL(caxpby(c->gz[k], c->gz[j], n5, Ls, (float)-br, (float)-bi, 1.f, st), "caxpby");
             }
             double nn;
-            if ((s = dot_host(c, c->gw[k], c->gw[k], &nn, &bi, st))) return s;
+            if ((s = dot_host(c, c->gw[k], c->gw[k], &nn, &bi, st)) || (s = check_net(c))) return s;
+            float nms = 0.f;
+            CK(cudaEventElapsedTime(&nms, c->nev[0], c->nev[1]), "cudaEventElapsedTime");
+            c->net_ms += nms;
             if (!(nn > 0.0) || !std::isfinite(nn)) break;  // no new direction: fall back below
             const float sc = (float)(1.0 / std::sqrt(nn));
             CKL(caxpby(c->gw[k], c->gw[k], n5, Ls, 0.f, 0.f, sc, st), "scale");
@@ -2196,7 +2222,7 @@ extern "C" eofa_status eofa_train_preconditioner(eofa_ctx* ctx, const void* cons
                                                  float* weights_out, eofa_train_stats* stats, void* stream) {
     if (!ctx || !sources || n_sources <= 0 || !init_weights || !opts || !weights_out) return EOFA_ERR_ARG;
     if (opts->pairs <= 0 || opts->snapshot_every <= 0 || opts->epochs <= 0 || opts->batch <= 0 || !(opts->lr > 0.0) ||
-        !(opts->solve_tol > 0.0))
+        !(opts->solve_tol > 0.0) || opts->holdout < 0)
         return EOFA_ERR_ARG;
     eofa_ctx* c = ctx;
     cudaStream_t st = (cudaStream_t)stream;
@@ -2208,7 +2234,7 @@ extern "C" eofa_status eofa_train_preconditioner(eofa_ctx* ctx, const void* cons
     const Geom& g = c->g;
     const long V = 2L * g.Vh, n5 = c->n5;
     const int Ls = g.Ls, B = opts->batch;
-    const int P = opts->pairs;
+    const int P = opts->pairs + opts->holdout;  // training pairs, then the held-out ones
     // the loss reduction shares the context's reduction buffers, sized for
     // one half-lattice 5D field: a batch holds at most Ls/2 full-lattice slices
     if (2L * B > Ls) return fail(c, EOFA_ERR_ARG, "train batch must be at most Ls/2");
@@ -2287,23 +2313,49 @@ extern "C" eofa_status eofa_train_preconditioner(eofa_ctx* ctx, const void* cons
         }
     }
     if (have == 0) return fail(c, EOFA_ERR_ARG, "no training pairs (zero sources?)");
+    const int ntrain = std::min(have, opts->pairs);
+    const int nhold = have - ntrain;
+    const ConvGeom cgB = conv_geom_of(c, B);
+    std::vector<float> hw(B);
+    // mean relative squared error of the current weights on pairs first .. first + count - 1
+    auto eval_loss = [&](int first, int count, double* out) -> eofa_status {
+        double sum = 0.0;
+        for (int b0 = 0; b0 < count; b0 += B) {
+            for (int b = 0; b < B; ++b) {
+                const bool use = b0 + b < count;
+                const int p = first + (use ? b0 + b : 0);
+                CK(cudaMemcpyAsync(a0 + (size_t)b * V * kCP, pr + (size_t)p * V * kCP, sizeof(bf16) * V * kCP,
+                                   cudaMemcpyDeviceToDevice, st), "batch");
+                CK(cudaMemcpyAsync(et + (size_t)b * V * kCP, pe + (size_t)p * V * kCP, sizeof(bf16) * V * kCP,
+                                   cudaMemcpyDeviceToDevice, st), "batch");
+                hw[b] = use ? pw[p] : 0.f;
+            }
+            CK(cudaMemcpyAsync(wdev, hw.data(), sizeof(float) * B, cudaMemcpyHostToDevice, st), "weights");
+            CK(net_forward(c->net, cgB, a0, a1, a2, o32, st), "forward");
+            CK(loss_grad(o32, et, wdev, dout, g, B, red(c, FIN_STORE, 4), st), "loss");
+            if ((s = read_scal(c, st))) return s;
+            sum += c->h_scal->store[4] * B;
+        }
+        *out = count > 0 ? sum / count : 0.0;
+        return EOFA_OK;
+    };
+    double hold_init = 0.0, hold_final = 0.0;
+    if (nhold > 0 && (s = eval_loss(ntrain, nhold, &hold_init))) return s;
 
     // ---- Adam on the relative squared error ----
-    std::vector<int> perm(have);
-    for (int i = 0; i < have; ++i) perm[i] = i;
+    std::vector<int> perm(ntrain);
+    for (int i = 0; i < ntrain; ++i) perm[i] = i;
     unsigned long long lcg = 0x9e3779b97f4a7c15ull;  // fixed-seed shuffle of the pair order
-    for (int i = have - 1; i > 0; --i) {
+    for (int i = ntrain - 1; i > 0; --i) {
         lcg = lcg * 6364136223846793005ull + 1442695040888963407ull;
         const int k = (int)((lcg >> 33) % (unsigned long long)(i + 1));
         std::swap(perm[i], perm[k]);
     }
-    const int steps = std::max(1, (int)((long)opts->epochs * have / B));
-    const ConvGeom cgB = conv_geom_of(c, B);
-    std::vector<float> hw(B);
+    const int steps = std::max(1, (int)((long)opts->epochs * ntrain / B));
     double loss_first = 0.0, loss_last = 0.0;
     for (int step = 0; step < steps; ++step) {
         for (int b = 0; b < B; ++b) {
-            const int p = perm[((long)step * B + b) % have];
+            const int p = perm[((long)step * B + b) % ntrain];
             CK(cudaMemcpyAsync(a0 + (size_t)b * V * kCP, pr + (size_t)p * V * kCP, sizeof(bf16) * V * kCP,
                                cudaMemcpyDeviceToDevice, st), "batch");
             CK(cudaMemcpyAsync(et + (size_t)b * V * kCP, pe + (size_t)p * V * kCP, sizeof(bf16) * V * kCP,
@@ -2324,11 +2376,16 @@ extern "C" eofa_status eofa_train_preconditioner(eofa_ctx* ctx, const void* cons
             if (step == 0) loss_last = loss_first;
         }
     }
+    if (nhold > 0 && (s = eval_loss(ntrain, nhold, &hold_final))) return s;
     CK(cudaMemcpyAsync(weights_out, c->net.Wm, sizeof(float) * kNetWeights, cudaMemcpyDeviceToHost, st), "download");
     CK(cudaStreamSynchronize(st), "sync");
+    if ((s = check_net(c))) return s;
     c->net_ready = true;
     if (stats) {
-        stats->pairs = have;
+        stats->holdout_pairs = nhold;
+        stats->holdout_loss_init = hold_init;
+        stats->holdout_loss_final = hold_final;
+        stats->pairs = ntrain;
         stats->steps = steps;
         stats->solves = solves;
         stats->loss_first = loss_first;

@@ -2,16 +2,12 @@
 // implicit GEMMs on the BF16 tensor cores (FP32 accumulate), their two
 // backward passes, activation packing and Adam.
 //
-// Forward (and backward-data, which is the same product with the mirrored,
-// transposed weights): a CTA owns 128 output sites x 32 output channels;
-// the K loop runs over the 81 taps x 32 input channels.  Per tap the 128
-// neighbour rows (64 bytes of BF16 channels each) and the tap's 32x32
-// weight block are brought to shared memory with cp.async, double buffered,
-// in an XOR-swizzled layout that ldmatrix reads without bank conflicts; each
-// of the 4 warps runs mma.m16n8k16 on 32 sites x 32 channels.
+// Forward and backward-data (the same product with the mirrored, transposed
+// weights): k_conv_tc, on the 5th-generation tensor cores (tcgen05.mma, the
+// accumulator in tensor memory), described at the kernel.
 // Backward-weights: a CTA owns one tap and a chunk of sites; the product
-// dW[tap] = dY^T in_shift (32 x 32, K = sites) is accumulated per warp and
-// reduced into the FP32 gradient with atomics.
+// dW[tap] = dY^T in_shift (32 x 32, K = sites) is accumulated per warp with
+// mma.sync and reduced into the FP32 gradient with atomics.
 #include "learned.h"
 
 namespace eofa {
@@ -23,6 +19,11 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
 }
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(sdst)), "l"(gsrc));
+}
+// L1-allocating copy: the neighbour rows of consecutive taps overlap
+// almost entirely within a CTA's 128 rows, so they are served from L1
+__device__ __forceinline__ void cp_async16_ca(void* sdst, const void* gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(sdst)), "l"(gsrc));
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
@@ -72,104 +73,210 @@ __device__ __forceinline__ int shifted_site(const ConvGeom& g, const Coord& c, i
 
 enum Epi { EPI_LEAKY_BF16 = 0, EPI_F32 = 1, EPI_DMASK_BF16 = 2 };
 
-template <int EPI>
-__global__ void __launch_bounds__(128) k_conv(const bf16* __restrict__ in, const bf16* __restrict__ W,
-                                              void* __restrict__ out, const bf16* __restrict__ mask, ConvGeom g) {
-    __shared__ __align__(128) bf16 sA[2][128 * 32];
-    __shared__ __align__(128) bf16 sB[2][32 * 32];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+// ---------------------------------------------------------------------------
+// The convolution on the 5th-generation tensor cores (tcgen05).
+//
+// A CTA owns 128 output rows (sites) x 32 output channels: the accumulator
+// is a 128-lane x 32-column FP32 block of tensor memory (TMEM), allocated by
+// warp 0.  Per tap, the 128 neighbour rows (32 BF16 channels each) and the
+// tap's 32 x 32 weight block are copied with cp.async (the rows through L1:
+// consecutive taps of a CTA read almost the same rows) into shared memory in
+// the tensor cores' canonical K-major layout without swizzle: 8-row x
+// 16-byte core matrices, 128 bytes apart along K and 512 bytes apart along
+// M (N); two buffers, so the copies of tap t+1 overlap the MMAs of tap t.
+// One thread issues the tap's two M128 x N32 x K16 MMAs (kind::f16, BF16 in,
+// FP32 accumulate) and commits them to the buffer's mbarrier, which frees
+// the buffer for tap t+2.  The epilogue: each warp reads its 32 TMEM lanes
+// (its threads' rows) with tcgen05.ld.  Every mbarrier wait is bounded; on
+// expiry the CTA records the event in tc_fault, skips its output, frees
+// its tensor memory and returns.
+// ---------------------------------------------------------------------------
+__device__ int g_tc_fault;  // set when a bounded wait of the tcgen05 convolution expired
+
+constexpr int kTcStageA = 128 * 64;  // bytes of one A buffer (128 rows x 32 BF16)
+constexpr int kTcStageB = 32 * 64;   // bytes of one B buffer (32 rows x 32 BF16)
+// dynamic shared memory of an NST-buffer ring: buffers, NST mbarriers, the TMEM address
+constexpr int tc_smem_bytes(int nst) { return nst * (kTcStageA + kTcStageB) + 8 * nst + 16; }
+constexpr long kTcSpin = 1L << 22;   // mbarrier polls before a wait counts as expired
+
+// byte offset of 16-byte chunk q (K elements 8q..8q+7) of row r in a
+// canonical no-swizzle K-major tile with 4 core matrices along K
+__device__ __forceinline__ int tc_off(int r, int q) { return ((r >> 3) * 4 + q) * 128 + (r & 7) * 16; }
+
+// shared-memory matrix descriptor: start, leading (K) and stride (M/N)
+// byte offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ unsigned long long tc_desc(unsigned saddr) {
+    const unsigned long long lbo = 128, sbo = 512;
+    return (unsigned long long)((saddr >> 4) & 0x3FFF) | (((lbo >> 4) & 0x3FFF) << 16) |
+           (((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+// instruction descriptor: D FP32, A and B BF16, both K-major, N = 32, M = 128
+constexpr unsigned kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mbar_init(unsigned a, unsigned n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(n) : "memory");
+}
+// true when the phase of the given parity has completed; gives up after kTcSpin polls
+__device__ __forceinline__ bool mbar_wait(unsigned a, unsigned parity) {
+    for (long i = 0; i < kTcSpin; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <int EPI, int NST>
+__global__ void __launch_bounds__(128) k_conv_tc(const bf16* __restrict__ in, const bf16* __restrict__ W,
+                                                 void* __restrict__ out, const bf16* __restrict__ mask, ConvGeom g) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char* sA = tc_smem;                         // [NST][kTcStageA]
+    unsigned char* sB = tc_smem + NST * kTcStageA;       // [NST][kTcStageB]
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(sB + NST * kTcStageB);  // [NST]
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(bar + NST);
+    __shared__ int s_fault;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const long rows = (long)g.V * g.S;
-    const long g0 = (long)blockIdx.x * 128;
-    const long gi = g0 + tid;
+    const long gi = (long)blockIdx.x * 128 + tid;
     const bool rv = gi < rows;
     const int sl = rv ? (int)(gi / g.V) : 0;
     const int site = rv ? (int)(gi - (long)sl * g.V) : 0;
     const Coord c = coord_of(g, site);
 
+    if (tid == 0) {
+        for (int b = 0; b < NST; ++b) mbar_init(smem_u32(bar + b), 1);
+        s_fault = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = *tmem_slot;
+
     auto load_tap = [&](int tap, int buf) {
-        bf16* arow = sA[buf];
+        unsigned char* a = sA + buf * kTcStageA;
         if (rv) {
             const int ns = shifted_site(g, c, tap);
             const bf16* src = in + ((long)sl * g.V + ns) * kCP;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) cp_async16(arow + swz(tid, q), src + q * 8);
+            for (int q = 0; q < 4; ++q) cp_async16_ca(a + tc_off(tid, q), src + q * 8);
         } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                *reinterpret_cast<uint4*>(arow + swz(tid, q)) = make_uint4(0u, 0u, 0u, 0u);
+            for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(a + tc_off(tid, q)) = make_uint4(0u, 0u, 0u, 0u);
         }
         const int wr = tid >> 2, wq = tid & 3;
-        cp_async16(sB[buf] + swz(wr, wq), W + ((long)tap * 32 + wr) * 32 + wq * 8);
+        cp_async16(sB + buf * kTcStageB + tc_off(wr, wq), W + ((long)tap * 32 + wr) * 32 + wq * 8);
         cp_commit();
     };
 
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
-
-    load_tap(0, 0);
+    // ring of NST buffers: taps 0 .. NST-2 are in flight before the first
+    // MMA; tap t + NST - 1 goes into the buffer of tap t - 1 once the MMAs
+    // of tap t - 1 have been committed as complete.  Tap t is the
+    // (t / NST)-th commit on bar[t % NST] (phase parity (t / NST) & 1).
+    bool ok = true;
+    for (int t = 0; t < NST - 1; ++t) load_tap(t, t);
     for (int tap = 0; tap < 81; ++tap) {
-        if (tap + 1 < 81) {
-            load_tap(tap + 1, (tap + 1) & 1);
-            cp_wait<1>();
+        const int buf = tap % NST;
+        const int nx = tap + NST - 1;
+        if (nx < 81) {
+            if (tap >= 1) {
+                const int pt = tap - 1;
+                if (!mbar_wait(smem_u32(bar + pt % NST), (pt / NST) & 1)) ok = false;
+            }
+            load_tap(nx, nx % NST);
+            cp_wait<NST - 1>();
         } else {
             cp_wait<0>();
         }
+        // this thread's copies of tap's buffer are visible to the tensor cores
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        const bf16* A = sA[tap & 1];
-        const bf16* B = sB[tap & 1];
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned a0 = smem_u32(sA + buf * kTcStageA), b0 = smem_u32(sB + buf * kTcStageB);
 #pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-            unsigned af[2][4], bfr[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r = warp * 32 + mt * 16 + (lane & 15);
-                ldsm_x4(af[mt], A + swz(r, ks * 2 + (lane >> 4)));
+            for (int h = 0; h < 2; ++h) {
+                const unsigned long long ad = tc_desc(a0 + h * 256), bd = tc_desc(b0 + h * 256);
+                const unsigned acc = (tap > 0 || h > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc)
+                    : "memory");
             }
-#pragma unroll
-            for (int np = 0; np < 2; ++np) {
-                const int r = np * 16 + (lane & 7) + ((lane >> 4) << 3);
-                ldsm_x4(bfr[np], B + swz(r, ks * 2 + ((lane >> 3) & 1)));
-            }
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt)
-                    mma16816(acc[mt][nt], af[mt], bfr[nt >> 1][(nt & 1) * 2], bfr[nt >> 1][(nt & 1) * 2 + 1]);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(bar + buf))
+                         : "memory");
         }
-        __syncthreads();
     }
-    // epilogue: accumulator (row lane/4 [+8], cols 2*(lane%4) [+1]) of each tile
+    // the last commit covers every MMA of the CTA
+    if (!mbar_wait(smem_u32(bar + 80 % NST), (80 / NST) & 1)) ok = false;
+    if (!ok) s_fault = 1;
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!s_fault) {
+        unsigned r[32];
+        const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+              "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+              "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (rv) {
+            if constexpr (EPI == EPI_F32) {
+                float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + gi * kCP);
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
+                for (int q = 0; q < 8; ++q)
+                    o[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                       __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+            } else {
+                uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(out) + gi * kCP);
+                const uint4* mk = reinterpret_cast<const uint4*>(mask + gi * kCP);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const long go = g0 + warp * 32 + mt * 16 + (lane >> 2) + h * 8;
-            if (go >= rows) continue;
+                for (int q = 0; q < 4; ++q) {
+                    uint4 mq = make_uint4(0u, 0u, 0u, 0u);
+                    if constexpr (EPI == EPI_DMASK_BF16) mq = mk[q];
+                    const unsigned* mw = reinterpret_cast<const unsigned*>(&mq);
+                    unsigned w[4];
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const int col = nt * 8 + (lane & 3) * 2;
-                float v0 = acc[mt][nt][h * 2], v1 = acc[mt][nt][h * 2 + 1];
-                if constexpr (EPI == EPI_F32) {
-                    *reinterpret_cast<float2*>(reinterpret_cast<float*>(out) + go * kCP + col) = make_float2(v0, v1);
-                } else {
-                    if constexpr (EPI == EPI_LEAKY_BF16) {
-                        v0 = v0 > 0.f ? v0 : kLeaky * v0;
-                        v1 = v1 > 0.f ? v1 : kLeaky * v1;
-                    } else {
-                        const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(mask + go * kCP + col);
-                        v0 *= __bfloat162float(m.x) > 0.f ? 1.f : kLeaky;
-                        v1 *= __bfloat162float(m.y) > 0.f ? 1.f : kLeaky;
+                    for (int e = 0; e < 4; ++e) {
+                        float v0 = __uint_as_float(r[8 * q + 2 * e]), v1 = __uint_as_float(r[8 * q + 2 * e + 1]);
+                        if constexpr (EPI == EPI_LEAKY_BF16) {
+                            v0 = v0 > 0.f ? v0 : kLeaky * v0;
+                            v1 = v1 > 0.f ? v1 : kLeaky * v1;
+                        } else {
+                            const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(&mw[e]);
+                            v0 *= __bfloat162float(m.x) > 0.f ? 1.f : kLeaky;
+                            v1 *= __bfloat162float(m.y) > 0.f ? 1.f : kLeaky;
+                        }
+                        const __nv_bfloat162 b = __floats2bfloat162_rn(v0, v1);
+                        w[e] = *reinterpret_cast<const unsigned*>(&b);
                     }
-                    *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<bf16*>(out) + go * kCP + col) =
-                        __floats2bfloat162_rn(v0, v1);
+                    o[q] = make_uint4(w[0], w[1], w[2], w[3]);
                 }
             }
         }
+    } else if (tid == 0) {
+        atomicExch(&g_tc_fault, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
 // dW[tap][co][ci] += sum_rows dy[row][co] * in[shift(row, tap)][ci]
@@ -324,11 +431,14 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
 
 inline int blocks_for(long n, int bt) { return (int)((n + bt - 1) / bt); }
 
+constexpr int kTcStages = 2;  // deeper rings measured no faster
+
 template <int EPI>
 cudaError_t conv(const bf16* in, const bf16* W, void* out, const bf16* mask, const ConvGeom& g, cudaStream_t st) {
     const long rows = (long)g.V * g.S;
     if (rows == 0) return cudaSuccess;
-    k_conv<EPI><<<blocks_for(rows, 128), 128, 0, st>>>(in, W, out, mask, g);
+    static_assert(tc_smem_bytes(kTcStages) <= 48 * 1024, "no opt-in shared memory needed");
+    k_conv_tc<EPI, kTcStages><<<blocks_for(rows, 128), 128, tc_smem_bytes(kTcStages), st>>>(in, W, out, mask, g);
     return cudaGetLastError();
 }
 
@@ -380,6 +490,16 @@ cudaError_t net_backward(const NetDev& n, const ConvGeom& g, const bf16* a0, con
     if ((e = wgrad(a0, d1, dW0, g, kNetCout[0], kNetCin[0], st)) != cudaSuccess) return e;
     if (din) return conv<EPI_F32>(d1, n.Wb[0], din, nullptr, g, st);
     return cudaSuccess;
+}
+
+cudaError_t net_fault(int* fault) {
+    // read and clear the flag the convolution sets when a bounded wait expired
+    cudaError_t e = cudaMemcpyFromSymbol(fault, g_tc_fault, sizeof(int));
+    if (e == cudaSuccess && *fault) {
+        const int zero = 0;
+        e = cudaMemcpyToSymbol(g_tc_fault, &zero, sizeof(int));
+    }
+    return e;
 }
 
 cudaError_t pack_act(const float* in24, bf16* a32, long rows, cudaStream_t st) {

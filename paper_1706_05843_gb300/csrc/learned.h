@@ -50,6 +50,10 @@ cudaError_t net_forward(const NetDev& n, const ConvGeom& g, const bf16* a0, bf16
 cudaError_t net_backward(const NetDev& n, const ConvGeom& g, const bf16* a0, const bf16* a1, const bf16* a2,
                          const float* dout, float* dW, float* din, bf16* dob, bf16* d1, bf16* d2,
                          cudaStream_t st);
+// after a synchronisation: *fault = 1 (and the flag cleared) when a
+// convolution gave up on a bounded wait and skipped its output since the
+// last call; the results computed meanwhile are not valid
+cudaError_t net_fault(int* fault);
 // FP32 [S][V][24] <-> BF16/FP32 [S][V][32]
 cudaError_t pack_act(const float* in24, bf16* a32, long rows, cudaStream_t st);
 cudaError_t unpack_out(const float* out32, float* out24, long rows, cudaStream_t st);

@@ -48,7 +48,9 @@ def test_struct_layouts():
     # sizes implied by include/eofa.h on LP64
     assert C.sizeof(B.eofa_params) == 4 * 4 + 4 + 4 + 7 * 8 + 4 + 4
     assert C.sizeof(B.eofa_solve_opts) == 8 + 4 + 4 + 8 + 6 * 4 + 8
-    assert C.sizeof(B.eofa_solve_stats) == 4 * 4 + 5 * 8 + 8 + 2 * 4
+    assert C.sizeof(B.eofa_solve_stats) == 4 * 4 + 5 * 8 + 8 + 2 * 4 + 8
+    assert C.sizeof(B.eofa_train_opts) == 4 * 4 + 2 * 8 + 8      # holdout + tail padding
+    assert C.sizeof(B.eofa_train_stats) == 3 * 4 + 4 + 3 * 8 + 4 + 4 + 2 * 8   # with alignment padding
 
 
 def test_status_strings(libeofa):
