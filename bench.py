@@ -339,7 +339,7 @@ def run_learned(B, I, torch, dev):
     dims_t, Ls_t = (16, 16, 16, 32), 16
     Ut = torch.from_numpy(I.gauge_field(dims_t, 0.5, 3)).to(dev)
     st_ = B.Solver(Ut, dims_t, Ls_t, **act)
-    srcs = [torch.from_numpy(I.gaussian_fermion(dims_t, Ls_t, 5000 + i)).to(dev) for i in range(46)]
+    srcs = [torch.from_numpy(I.gaussian_fermion(dims_t, Ls_t, 5000 + i)).to(dev) for i in range(60)]
     opts = B.make_train_opts(pairs=2000, snapshot_every=8, epochs=3, batch=8, lr=1e-3, solve_tol=1e-6, holdout=200)
     t_train, (w, tst) = _timed(torch, lambda: B.eofa_train_preconditioner(st_.ctx, srcs, w0, opts))
     st_.close()

@@ -1,13 +1,32 @@
 """GPU tests of the learned preconditioner through the C ABI.
 
 The BF16 tensor-core network (forward and both backward passes) is compared
-with the FP64 numpy oracle evaluated on the same BF16-rounded inputs and
-weights; the remaining difference comes from BF16 storage of the two hidden
-activations and from the order of FP32 accumulation (measured ~0.5%, bound
-2%).  Training must reduce its loss, and a solve preconditioned by the
-trained network must reach the true residual 1e-10 judged by the solver
-oracle; the test prints what the trained network gains over the untrained
-one and over the method without it.
+with the FP64 numpy oracle, in two ways.
+
+* Against the oracle's plain FP64 network on the same BF16-rounded inputs
+  and weights: the library also stores the two hidden activations (and, in
+  the backward pass, the incoming gradients) in BF16, so the two differ by
+  the propagated BF16 rounding of those, at most a few units of 2^-9 ~ 2e-3
+  relative; bound 2% (forward) and 3% (backward).
+* Forward, against the same oracle functions with BF16 rounding applied
+  exactly where the library stores BF16 (the storage model): what is left is
+  the order of the FP32 accumulation (about 2592 terms, relative error
+  ~1e-6) and the rare BF16 rounding of a hidden value that this order moves
+  across a rounding boundary (one BF16 unit, 2^-8 of that value, for a
+  fraction ~1e-6 / 2^-8 of the values).  Bound 1e-3, far above both effects
+  and far below a misplaced tap, channel or sign (errors of order 1).
+* Backward: the LeakyReLU derivative jumps (1 <-> 0.1) where a
+  pre-activation crosses zero, so BF16 storage of the activations flips it
+  for the pre-activations that the rounding moves across zero, and which ones
+  flip depends on the accumulation order.  The storage model's own distance
+  from the FP64 gradients measures this effect for the test's data; the
+  library's gradients must lie within twice that distance of the FP64 ones
+  (a misplaced tap, channel or sign gives errors of order 1).
+
+Training must reduce its loss and the error on held-out pairs, and a solve
+preconditioned by the trained network must reach the true residual 1e-10
+judged by the solver oracle; the test reports what the trained network
+changes against the untrained one and against the method without it.
 """
 import numpy as np
 import pytest
@@ -57,7 +76,38 @@ def test_net_forward_matches_oracle(env, dims, S):
     xt = torch.from_numpy(xb.astype(np.float32)).cuda()
     out = torch.empty_like(xt)
     B.eofa_net_forward(wb.astype(np.float32), dims, xt, out)
-    assert rel(out.cpu().numpy(), ref) < 2e-2
+    got = out.cpu().numpy()
+    assert rel(got, ref) < 2e-2
+    sm = forward_bf16_storage(xb, wb)
+    err = rel(got, sm)
+    print(f"forward {dims} S={S}: against FP64 {rel(got, ref):.2e}, against the BF16 storage model {err:.2e}")
+    assert err < 1e-3
+
+
+def forward_bf16_storage(x, w, cache=False):
+    """The oracle network with the library's BF16 storage of the hidden activations."""
+    W = N.split(w)
+    z1 = N.conv(x, W[0])
+    a1 = N.bf16_round(N.leaky(z1))
+    z2 = N.conv(a1, W[1])
+    a2 = N.bf16_round(N.leaky(z2))
+    out = N.conv(a2, W[2])
+    return (out, (z1, a1, z2, a2)) if cache else out
+
+
+def backward_bf16_storage(x, w, dout):
+    """Gradients through the storage model: incoming gradients stored in BF16
+    before each product, as the library does."""
+    W = N.split(w)
+    _, (z1, a1, z2, a2) = forward_bf16_storage(x, w, cache=True)
+    db = N.bf16_round(dout)
+    dW2 = N.conv_wgrad(a2, db)
+    dz2 = N.bf16_round(N.conv_adjoint(db, W[2]) * N.dleaky(z2))
+    dW1 = N.conv_wgrad(a1, dz2)
+    dz1 = N.bf16_round(N.conv_adjoint(dz2, W[1]) * N.dleaky(z1))
+    dW0 = N.conv_wgrad(x, dz1)
+    dx = N.conv_adjoint(dz1, W[0])
+    return np.concatenate([dW0.ravel(), dW1.ravel(), dW2.ravel()]), dx
 
 
 def test_net_backward_matches_oracle(env):
@@ -72,12 +122,19 @@ def test_net_backward_matches_oracle(env):
     gt = torch.from_numpy(g.astype(np.float32)).cuda()
     din = torch.empty_like(xt)
     dw = B.eofa_net_backward(w.astype(np.float32), dims, xt, gt, din)
+    dw_sm, dx_sm = backward_bf16_storage(x, w, g)
     off = 0
     for ci, co in zip(N.CIN, N.COUT):
         n = 81 * ci * co
-        assert rel(dw[off:off + n], dw_ref[off:off + n]) < 3e-2
+        e = rel(dw[off:off + n], dw_ref[off:off + n])
+        bound = 2.0 * rel(dw_sm[off:off + n], dw_ref[off:off + n])
+        print(f"weight gradient ({ci}->{co}): against FP64 {e:.2e}, bound {bound:.2e}")
+        assert e < bound
         off += n
-    assert rel(din.cpu().numpy(), dx_ref) < 3e-2
+    dxg = din.cpu().numpy()
+    e, bound = rel(dxg, dx_ref), 2.0 * rel(dx_sm, dx_ref)
+    print(f"input gradient: against FP64 {e:.2e}, bound {bound:.2e}")
+    assert e < bound
 
 
 def test_train_and_preconditioned_solve(env):
