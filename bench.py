@@ -297,13 +297,12 @@ def run_heatbath(B, I, torch, dev, solver):
     for fc in (0, 4):
         dt, (phi, st) = _timed(torch, lambda: solver.heatbath(eta, m1, m2, r, forecast=fc, tol=TOL, inner="f32"))
         mphi, _ = solver.apply_meofa(phi, m1, m2, tol=1e-12, inner="f32")
-        out[f"forecast_{fc}"] = {"s": dt, "eps": H.heatbath_error(eta, phi, mphi),
+        out[f"forecast_{fc}"] = {"s": dt, "eps": H.heatbath_error(solver, eta, phi, mphi),
                                  "inner_iters": [x.inner_iters for x in st],
                                  "max_true_res": max(x.true_res for x in st)}
     # the pseudofermion force of S = phi^dag M_EOFA phi at the drawn phi (Eq. eofa_force)
     dt, (f, st) = _timed(torch, lambda: solver.force(phi, m1, m2, tol=TOL, inner="f32"))
-    from paper_1706_05843_gb300.forces import force_norms
-    f_rms, f_max = force_norms(f)
+    f_rms, f_max = solver.force_norms(f)
     out["force"] = {"s": dt, "inner_iters": [x.inner_iters for x in st], "F_RMS": f_rms, "F_max": f_max}
     return out
 

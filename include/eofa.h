@@ -177,16 +177,19 @@ eofa_status eofa_solve(eofa_ctx *ctx, const void *rhs, void *sol,
                        void *stream);
 
 /* eofa_solve with the right-hand side and the solution in HOST memory
- * (complex128, same layout): the call copies rhs to the device, solves, and
- * copies the solution back, all on `stream`, and returns when the solution
- * is in `sol`.  The device copies live in two 5D work fields that the
- * context allocates on first use and keeps (the same ones the action calls
- * use).  Page-locked host buffers give the full copy bandwidth; pageable ones
- * work too.  With opts->use_guess, sol holds the initial guess on entry.  The
- * solution is copied back for every status the solver itself returns
- * (EOFA_OK, EOFA_ERR_NOT_CONVERGED, EOFA_ERR_TIMEOUT, EOFA_ERR_NONFINITE);
- * argument and CUDA errors leave sol untouched.  End-to-end entry of the
- * solve as Sec. V.A describes it (the paper has no separate host form). */
+ * (complex128, same layout), on `stream`; returns when the solution is in
+ * `sol`.  When both buffers are page-locked (cudaHostAlloc,
+ * cudaHostRegister, torch pin_memory) the solver's import and export kernels
+ * read rhs and write sol in place through their device mapping (over
+ * NVLink-C2C on a Grace-Blackwell node), with no staging copies.  Otherwise
+ * the call copies rhs to the device, solves and copies the solution back,
+ * through two 5D work fields that the context allocates on first use and
+ * keeps (the same ones the action calls use).  With opts->use_guess, sol
+ * holds the initial guess on entry.  On the staging path the solution is
+ * copied back for every status the solver itself returns (EOFA_OK,
+ * EOFA_ERR_NOT_CONVERGED, EOFA_ERR_TIMEOUT, EOFA_ERR_NONFINITE) and argument
+ * and CUDA errors leave sol untouched.  End-to-end entry of the solve as
+ * Sec. V.A describes it (the paper has no separate host form). */
 eofa_status eofa_solve_host(eofa_ctx *ctx, const double *rhs, double *sol,
                             const eofa_solve_opts *opts, eofa_solve_stats *stats,
                             void *stream);
@@ -261,6 +264,24 @@ eofa_status eofa_heatbath(eofa_ctx *ctx, double m1, double m2, int np, const dou
  * after the work has finished. */
 eofa_status eofa_force(eofa_ctx *ctx, double m1, double m2, const void *phi, void *force,
                        const eofa_solve_opts *opts, eofa_solve_stats *stats, void *stream);
+
+/* Force norms of Sec. VI (Eqs. L2_force, Linf_force) of a force in the layout
+ * eofa_force writes (device complex128 [t][z][y][x][mu][3][3] on the
+ * context's physical lattice): with ||F_mu(x)||^2 = sum_a (F^a_mu(x))^2 =
+ * 2 sum_ij |F_ij|^2 (Tr T^a T^b = -delta^ab / 2),
+ * f_rms = [sum_{x,mu} ||F_mu(x)||^2]^(1/2) / (4V) as printed and
+ * f_max = max_{x,mu} ||F_mu(x)||.  One pass over the force on the device;
+ * synchronises stream. */
+eofa_status eofa_force_norms(eofa_ctx *ctx, const void *force, double *f_rms, double *f_max,
+                             void *stream);
+
+/* <a, b> = sum_i conj(a_i) b_i over n complex128 elements of device arrays
+ * (FP64, summed in a fixed order: the same result every call), for the
+ * set-up and diagnostics around the solves (Rayleigh quotients, norms, the
+ * heatbath error of Eq. heatbath_rel_err).  Uses the context's reduction
+ * buffers; synchronises stream. */
+eofa_status eofa_dot(eofa_ctx *ctx, const void *a, const void *b, long n, double *re, double *im,
+                     void *stream);
 
 /* out[i] = K in[i] (dag = 0) or K^dag in[i] (dag = 1) for n contexts,
  * which may have different lattices. */

@@ -88,6 +88,8 @@ SIGNATURES = {
                             C.POINTER(eofa_solve_opts), C.POINTER(eofa_solve_stats), _vp], C.c_int),
     "eofa_solve_host": ([_vp, _dp, _dp, C.POINTER(eofa_solve_opts), C.POINTER(eofa_solve_stats), _vp], C.c_int),
     "eofa_measure_fma": ([C.c_int, C.c_int, _dp, _vp], C.c_int),
+    "eofa_dot": ([_vp, _vp, _vp, C.c_long, _dp, _dp, _vp], C.c_int),
+    "eofa_force_norms": ([_vp, _vp, _dp, _dp, _vp], C.c_int),
     "eofa_destroy": ([_vp], None),
     "eofa_apply_noalloc": ([C.POINTER(eofa_params), _vp, _vp, _vp, _vp], C.c_int),
     "eofa_net_forward": ([_fp, C.POINTER(C.c_int), C.c_int, _vp, _vp, _vp], C.c_int),
@@ -232,6 +234,22 @@ def eofa_measure_fma(prec, reps=5, stream=None):
     _check(None, lib().eofa_measure_fma(PREC[prec] if isinstance(prec, str) else int(prec), int(reps), C.byref(out),
                                         _stream(stream)))
     return out.value
+
+
+def eofa_dot(ctx, a, b, stream=None):
+    """<a, b> of two complex128 CUDA tensors of equal size, on the device (FP64)."""
+    if a.numel() != b.numel():
+        raise ValueError("eofa_dot needs fields of equal size")
+    re, im = C.c_double(0.0), C.c_double(0.0)
+    _check(ctx, lib().eofa_dot(ctx, _dptr(a), _dptr(b), int(a.numel()), C.byref(re), C.byref(im), _stream(stream)))
+    return complex(re.value, im.value)
+
+
+def eofa_force_norms(ctx, force, stream=None):
+    """(F_RMS, F_max) of a force from eofa_force, on the device."""
+    rms, mx = C.c_double(0.0), C.c_double(0.0)
+    _check(ctx, lib().eofa_force_norms(ctx, _dptr(force), C.byref(rms), C.byref(mx), _stream(stream)))
+    return rms.value, mx.value
 
 
 def eofa_set_system(ctx, m1, m2, m3, beta, pm):
@@ -446,6 +464,14 @@ class Solver:
         f = torch.empty((T, Z, Y, X, 4, 3, 3), dtype=torch.complex128, device="cuda")
         st = eofa_force(self.ctx, m1, m2, phi, f, make_opts(**opts), stream, check)
         return f, st
+
+    def dot(self, a, b, stream=None):
+        """<a, b> on the device (complex)."""
+        return eofa_dot(self.ctx, a, b, stream)
+
+    def force_norms(self, force, stream=None):
+        """(F_RMS, F_max) of a force from Solver.force (Sec. VI)."""
+        return eofa_force_norms(self.ctx, force, stream)
 
     def heatbath(self, eta, m1, m2, approx, pole_tol=None, forecast=0, stream=None, check=True, **opts):
         """M_EOFA(m1, m2)^(-1/2) eta with the rational approximation ``approx``

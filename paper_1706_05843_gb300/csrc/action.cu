@@ -339,6 +339,64 @@ cudaError_t multidot(const VecSet& set, const double* w, long n, double* partial
     return cudaGetLastError();
 }
 
+// Sec. VI force norms: per link ||F_mu(x)||^2 = 2 sum_ij |F_ij|^2 (the sum of
+// the squared generator components for Tr T^a T^b = -delta^ab / 2);
+// partial[b] = (sum, max) over block b's links, then one block combines them
+// in block order (deterministic)
+__global__ void __launch_bounds__(AT) k_force_norms(const double2* __restrict__ F, long nlinks,
+                                                    double2* __restrict__ partial) {
+    __shared__ double rs[AT / 32], rm[AT / 32];
+    double sum = 0.0, mx = 0.0;
+    for (long l = blockIdx.x * (long)AT + threadIdx.x; l < nlinks; l += (long)gridDim.x * AT) {
+        double n2 = 0.0;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            const double2 v = F[l * 9 + e];
+            n2 = fma(v.x, v.x, fma(v.y, v.y, n2));
+        }
+        n2 *= 2.0;
+        sum += n2;
+        mx = fmax(mx, n2);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sum += __shfl_down_sync(0xffffffffu, sum, o);
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) {
+        rs[wid] = sum;
+        rm[wid] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < AT / 32; ++k) {
+            a += rs[k];
+            b = fmax(b, rm[k]);
+        }
+        partial[blockIdx.x] = make_double2(a, b);
+    }
+}
+
+__global__ void k_force_norms_sum(const double2* __restrict__ partial, int nblk, double2* __restrict__ out) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < nblk; ++k) {
+        a += partial[k].x;
+        b = fmax(b, partial[k].y);
+    }
+    *out = make_double2(a, b);
+}
+
+cudaError_t force_norm_sums(const double* F, long nlinks, double* partial, double* out, cudaStream_t st) {
+    const int nb = multidot_blocks(nlinks);
+    k_force_norms<<<nb, AT, 0, st>>>((const double2*)F, nlinks, (double2*)partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_force_norms_sum<<<1, 1, 0, st>>>((const double2*)partial, nb, (double2*)out);
+    return cudaGetLastError();
+}
+
 cudaError_t combine(double* out, const VecSet& set, long n, cudaStream_t st) {
     k_combine<<<grid_of(n, 1 << 16), AT, 0, st>>>((double2*)out, set, n);
     return cudaGetLastError();

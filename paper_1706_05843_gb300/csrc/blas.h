@@ -78,6 +78,9 @@ cudaError_t omega_out(double* out4, const double* base4, double a, const double*
 // out[j] = <v_j, w> for j < set.n (n complex elements; partial holds
 // kMultiBlocks * kMultiMax complex values)
 cudaError_t multidot(const VecSet& set, const double* w, long n, double* partial, double* out, cudaStream_t st);
+// out[0] = sum over links of ||F_mu(x)||^2, out[1] = the largest one (n
+// links of 9 complex entries; partial holds kMultiBlocks complex values)
+cudaError_t force_norm_sums(const double* F, long nlinks, double* partial, double* out, cudaStream_t st);
 // out = sum_j set.c[j] set.v[j]
 cudaError_t combine(double* out, const VecSet& set, long n, cudaStream_t st);
 // EOFA force F[lex][mu] (3x3 complex, anti-Hermitian traceless) from the

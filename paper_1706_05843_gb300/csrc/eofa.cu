@@ -1277,6 +1277,16 @@ eofa_status solve_one(eofa_ctx* c, const double* rhs, double* sol, const eofa_so
     return s;
 }
 
+// the multi-dot partial sums and results of the context (allocated on first use)
+eofa_status ensure_mdot(eofa_ctx* c) {
+    if (c->mdot) return EOFA_OK;
+    void* p = nullptr;
+    eofa_status s = dalloc(c, &p, sizeof(double2) * (kMultiBlocks + 1) * kMultiMax);
+    if (s != EOFA_OK) return s;
+    c->mdot = (double*)p;
+    return EOFA_OK;
+}
+
 // Chronological initial guess (Sec. V.B): with the previous solutions psi_k
 // of the same term, x0 = sum_k c_k psi_k where
 // sum_k c_k psi_l^dag A psi_k = psi_l^dag rhs, A the current system (H form);
@@ -1289,12 +1299,8 @@ eofa_status forecast(eofa_ctx* c, double* const* prev, int n, const double* rhs,
     const long nc = c->n5 * 2 * 12;  // complex elements of a 5D field
     double* w = act_buf(c, 2);
     if (!w) return EOFA_ERR_OOM;
-    if (!c->mdot) {
-        void* p = nullptr;
-        eofa_status s = dalloc(c, &p, sizeof(double2) * (kMultiBlocks + 1) * kMultiMax);
-        if (s != EOFA_OK) return s;
-        c->mdot = (double*)p;
-    }
+    eofa_status s0 = ensure_mdot(c);
+    if (s0 != EOFA_OK) return s0;
     double* res = c->mdot + 2 * kMultiBlocks * kMultiMax;
     VecSet set{};
     set.n = n;
@@ -1637,6 +1643,20 @@ eofa_status eofa_solve_host(eofa_ctx* ctx, const double* rhs, double* sol, const
     eofa_ctx* c = ctx;
     c->err.clear();
     cudaStream_t st = (cudaStream_t)stream;
+    // page-locked host buffers: the import and export kernels read and write
+    // them in place (through NVLink-C2C on a Grace-Blackwell node), with no
+    // staging copies
+    cudaPointerAttributes ra{}, sa{};
+    const bool direct = cudaPointerGetAttributes(&ra, rhs) == cudaSuccess && ra.type == cudaMemoryTypeHost &&
+                        ra.devicePointer && cudaPointerGetAttributes(&sa, sol) == cudaSuccess &&
+                        sa.type == cudaMemoryTypeHost && sa.devicePointer;
+    cudaGetLastError();  // the queries of pageable pointers may leave an error behind
+    if (direct) {
+        eofa_status s = solve_impl(c, (const double*)ra.devicePointer, (double*)sa.devicePointer, *opts, stats, st);
+        if (stats) stats->status = s;
+        CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+        return s;
+    }
     double* drhs = act_buf(c, 0);
     double* dsol = act_buf(c, 1);
     if (!drhs || !dsol) return fail(c, EOFA_ERR_OOM, "work fields of the host solve");
@@ -1650,6 +1670,45 @@ eofa_status eofa_solve_host(eofa_ctx* ctx, const double* rhs, double* sol, const
         CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
     }
     return s;
+}
+
+eofa_status eofa_dot(eofa_ctx* ctx, const void* a, const void* b, long n, double* re, double* im, void* stream) {
+    if (!ctx || !a || !b || n < 0 || !re || !im) return EOFA_ERR_ARG;
+    eofa_ctx* c = ctx;
+    c->err.clear();
+    cudaStream_t st = (cudaStream_t)stream;
+    eofa_status s = ensure_mdot(c);
+    if (s != EOFA_OK) return s;
+    double* res = c->mdot + 2 * kMultiBlocks * kMultiMax;
+    VecSet set{};
+    set.n = 1;
+    set.v[0] = (const double2*)a;
+    CK(multidot(set, (const double*)b, n, c->mdot, res, st), "multidot");
+    double h[2];
+    CK(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    *re = h[0];
+    *im = h[1];
+    return EOFA_OK;
+}
+
+eofa_status eofa_force_norms(eofa_ctx* ctx, const void* force, double* f_rms, double* f_max, void* stream) {
+    if (!ctx || !force || !f_rms || !f_max) return EOFA_ERR_ARG;
+    eofa_ctx* c = ctx;
+    c->err.clear();
+    cudaStream_t st = (cudaStream_t)stream;
+    eofa_status s = ensure_mdot(c);
+    if (s != EOFA_OK) return s;
+    // links of the physical lattice (G-parity: the force is folded onto them)
+    const long nlinks = 4L * c->p.dims[0] * c->p.dims[1] * c->p.dims[2] * c->p.dims[3];
+    double* res = c->mdot + 2 * kMultiBlocks * kMultiMax;
+    CK(force_norm_sums((const double*)force, nlinks, c->mdot, res, st), "force_norm_sums");
+    double h[2];
+    CK(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    *f_rms = std::sqrt(h[0]) / (double)nlinks;
+    *f_max = std::sqrt(h[1]);
+    return EOFA_OK;
 }
 
 eofa_status eofa_set_system(eofa_ctx* ctx, double m1, double m2, double m3, double beta, int pm) {

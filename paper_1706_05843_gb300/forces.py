@@ -1,4 +1,7 @@
-"""Force norms of Sec. VI (Eqs. L2_force, Linf_force), host-side diagnostics.
+"""Force norms of Sec. VI (Eqs. L2_force, Linf_force): the definition for
+host arrays.  The library computes the same on the device from a force it
+produced (``Solver.force_norms``, eofa_force_norms), without copying the
+force to the host.
 
 For F_mu(x) = sum_a T^a F^a_mu(x) with Tr T^a T^b = -delta^ab / 2, the norm
 ||F_mu(x)|| = [sum_a (F^a_mu(x))^2]^(1/2) equals sqrt(2) times the Frobenius

@@ -12,37 +12,30 @@ module holds the set-up a caller performs around it:
     of the 2 N_p solves in turn, relax its tolerance while the heatbath error
     stays below a target.
 
-Inner products of the 4D fields are taken on the host in FP64: they are
-diagnostics of the set-up, not part of the solves.
+Inner products of the 4D fields are the solver's (``solver.dot``: the
+library's FP64 device reduction), so no field leaves the device.
 """
 from __future__ import annotations
 
-import numpy as np
+import math
 
 
-def _host(t) -> np.ndarray:
-    return t.detach().cpu().numpy().reshape(-1)
-
-
-def heatbath_error(eta, phi, m_phi) -> float:
+def heatbath_error(solver, eta, phi, m_phi) -> float:
     """epsilon = |eta^dag eta - phi^dag M_EOFA phi| / eta^dag eta."""
-    e, p, mp = _host(eta), _host(phi), _host(m_phi)
-    ee = np.vdot(e, e).real
-    return abs(ee - np.vdot(p, mp).real) / ee
+    ee = solver.dot(eta, eta).real
+    return abs(ee - solver.dot(phi, m_phi).real) / ee
 
 
 def largest_eigenvalue(solver, m1, m2, start, iters=12, **opts):
     """Power-iteration estimate of the largest eigenvalue of M_EOFA(m1, m2)
     (Hermitian positive definite), from the 4D field ``start``; returns
     (estimate, iterations' Rayleigh quotients)."""
-    import torch
-    v = start / float(torch.linalg.vector_norm(start))
+    v = start * (1.0 / math.sqrt(solver.dot(start, start).real))
     history = []
     for _ in range(iters):
         w, _ = solver.apply_meofa(v, m1, m2, **opts)
-        vh, wh = _host(v), _host(w)
-        history.append(np.vdot(vh, wh).real / np.vdot(vh, vh).real)
-        v = w / float(np.linalg.norm(wh))
+        history.append(solver.dot(v, w).real / solver.dot(v, v).real)
+        v = w * (1.0 / math.sqrt(solver.dot(w, w).real))
     return history[-1], history
 
 
@@ -52,7 +45,7 @@ def measure(solver, eta, m1, m2, approx, pole_tol=None, forecast=0, m_tol=1e-12,
     mopts = dict(opts)
     mopts["tol"] = m_tol
     m_phi, _ = solver.apply_meofa(phi, m1, m2, **mopts)
-    return phi, heatbath_error(eta, phi, m_phi), st
+    return phi, heatbath_error(solver, eta, phi, m_phi), st
 
 
 def tune_pole_tolerances(solver, eta, m1, m2, approx, eps_tol, tol=1e-10, factor=10.0, max_tol=1e-3,

@@ -100,6 +100,8 @@ def test_argument_errors_without_gpu(libeofa):
     assert libeofa.eofa_measure_fma(2, 3, C.byref(out), None) == 1   # FP16 has no FMA probe
     assert libeofa.eofa_measure_fma(0, 0, C.byref(out), None) == 1   # reps < 1
     assert libeofa.eofa_measure_fma(0, 3, None, None) == 1
+    assert libeofa.eofa_dot(None, None, None, 0, None, None, None) == 1
+    assert libeofa.eofa_force_norms(None, None, None, None, None) == 1
     # action calls without a context
     opts = B.make_opts(tol=1e-10)
     assert libeofa.eofa_set_system(None, 0.04, 1.0, 0.04, -1.0, 1) == 1

@@ -153,6 +153,9 @@ def test_heatbath_error(env, case):
         # the GPU's own M_EOFA gives the same epsilon
         mg, _ = s.apply_meofa(torch.from_numpy(phi).cuda(), M1, M2, tol=1e-12, inner="f32")
         assert abs(A.heatbath_error(eta, phi, mg.cpu().numpy()) - eps[n]) < 1e-10
+        # and the library's device inner products give it too
+        from paper_1706_05843_gb300 import heatbath as H
+        assert abs(H.heatbath_error(s, e, torch.from_numpy(phi).cuda(), mg) - eps[n]) < 1e-10
     assert eps[10] < 1e-10
     assert eps[3] > 1e3 * eps[10]
     s.close()

@@ -212,5 +212,5 @@ def test_fullsize_force_and_heatbath_properties(env):
     eta = phi
     out, st = s.heatbath(eta, m1, m2, r, forecast=4, tol=1e-11, inner="f32")
     mo, _ = s.apply_meofa(out, m1, m2, tol=1e-12, inner="f32")
-    assert H.heatbath_error(eta, out, mo) < 1e-9
+    assert H.heatbath_error(s, eta, out, mo) < 1e-9
     s.close()

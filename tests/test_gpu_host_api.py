@@ -1,9 +1,12 @@
-"""GPU tests of the host-buffer solve and the FMA throughput probe.
+"""GPU tests of the host-buffer solve, the device diagnostics and the FMA
+throughput probe.
 
 eofa_solve_host copies a host right-hand side in and the solution out inside
 the call; the answer must be the device solve's (the solver is
-deterministic, so bit for bit) and is judged by the oracle.  The FMA probe
-must report a positive throughput with FP32 above FP64.
+deterministic, so bit for bit) and is judged by the oracle.  eofa_dot must
+equal numpy's FP64 inner product (and repeat bit for bit), eofa_force_norms
+the Sec. VI definition evaluated on the host.  The FMA probe must report a
+positive throughput with FP32 above FP64.
 """
 import numpy as np
 import pytest
@@ -44,11 +47,18 @@ def test_solve_host_matches_device_solve(env, inner):
     assert st_h.status == 0 and st_h.inner_iters == st_d.inner_iters
     assert np.array_equal(host_sol.numpy(), dev.cpu().numpy())
     assert np.linalg.norm(phi - o.hsys(host_sol.numpy())) / np.linalg.norm(phi) <= 1e-10
+    # pageable buffers (the staging path) give the same answer
+    out_p = np.empty_like(phi)
+    _, st_p = s.solve_host(phi, out_p, tol=1e-10, inner=inner)
+    assert st_p.status == 0 and np.array_equal(out_p, host_sol.numpy())
     # pageable numpy buffers and the initial guess: restarting from the
     # converged answer needs no inner iteration
     out = host_sol.numpy().copy()
     _, st_g = s.solve_host(phi, out, tol=1e-10, inner=inner, use_guess=True)
     assert st_g.status == 0 and st_g.inner_iters == 0
+    # the same restart from page-locked buffers (the guess read in place)
+    _, st_gp = s.solve_host(host_rhs, host_sol, tol=1e-10, inner=inner, use_guess=True)
+    assert st_gp.status == 0 and st_gp.inner_iters == 0
     s.close()
 
 
@@ -68,3 +78,32 @@ def test_measure_fma(env):
     f32 = B.eofa_measure_fma("f32", reps=3)
     print(f"FMA throughput: FP64 {f64:.2f} TFLOP/s, FP32 {f32:.2f} TFLOP/s")
     assert 0.0 < f64 < f32
+
+
+def test_dot_matches_numpy(env):
+    torch, B, O = env
+    dims, Ls = (4, 4, 4, 4), 8
+    s = B.Solver(I.gauge_field(dims, 0.3, 1), dims, Ls, **ACT)
+    a = I.gaussian_fermion(dims, Ls, 21)
+    b = I.gaussian_fermion(dims, Ls, 22)
+    da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    ref = np.vdot(a.ravel(), b.ravel())
+    got = s.dot(da, db)
+    assert abs(got - ref) <= 1e-13 * abs(ref)
+    assert s.dot(da, db) == got                       # fixed summation order
+    assert abs(s.dot(da, da).real - np.vdot(a.ravel(), a.ravel()).real) <= 1e-13 * np.vdot(a.ravel(), a.ravel()).real
+    s.close()
+
+
+def test_force_norms_match_definition(env):
+    torch, B, O = env
+    from paper_1706_05843_gb300 import forces
+    dims, Ls = (4, 4, 4, 4), 8
+    s = B.Solver(I.gauge_field(dims, 0.3, 1), dims, Ls, **ACT)
+    phi = torch.from_numpy(I.heatbath_noise(dims, 31)).cuda()
+    f, _ = s.force(phi, ACT["m1"], ACT["m2"], tol=1e-10, inner="f32")
+    rms, mx = s.force_norms(f)
+    hrms, hmx = forces.force_norms(f.cpu().numpy())
+    assert rms == pytest.approx(hrms, rel=1e-13)
+    assert mx == pytest.approx(hmx, rel=1e-13)
+    s.close()

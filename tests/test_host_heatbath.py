@@ -27,6 +27,9 @@ class DenseSolver:
         self.noise = rng.standard_normal((64, n)) + 1j * rng.standard_normal((64, n))
         self.calls = 0
 
+    def dot(self, a, b):
+        return complex(np.vdot(a.numpy(), b.numpy()))
+
     def apply_meofa(self, phi, m1, m2, tol=1e-12, **_):
         self.calls += 1
         return torch.from_numpy(self.M @ phi.numpy()), [None, None]
@@ -59,9 +62,9 @@ def test_heatbath_error_definition():
     w, Q = np.linalg.eigh(s.M)
     exact = Q @ ((Q.conj().T @ eta.numpy()) / np.sqrt(w))
     phi = torch.from_numpy(exact)
-    assert H.heatbath_error(eta, phi, s.apply_meofa(phi, 0, 0)[0]) < 1e-13
+    assert H.heatbath_error(s, eta, phi, s.apply_meofa(phi, 0, 0)[0]) < 1e-13
     bad = torch.from_numpy(1.01 * exact)
-    assert abs(H.heatbath_error(eta, bad, s.apply_meofa(bad, 0, 0)[0]) - (1.01 ** 2 - 1)) < 1e-12
+    assert abs(H.heatbath_error(s, eta, bad, s.apply_meofa(bad, 0, 0)[0]) - (1.01 ** 2 - 1)) < 1e-12
 
 
 def test_tune_pole_tolerances():
