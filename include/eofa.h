@@ -290,7 +290,17 @@ eofa_status eofa_apply_batched(eofa_ctx *const *ctx, int n, const void *const *i
 
 /* n independent solves (one per context and rhs), possibly of different
  * lattice sizes; stats is an array of n entries (or NULL).  Returns the
- * first non-OK status. */
+ * first non-OK status.  The mixed-precision defect correction of Sec. IV
+ * (Eq. generic_eofa_system solved on the even-odd Schur complement, FP64
+ * outer residual and update, inner CGNR in opts->inner) of all n systems is
+ * one CUDA graph launch: each system's outer decision (converged, caps,
+ * deadline, non-finite) and inner restart are taken on the device, so the
+ * systems advance independently and the host waits once.  The graph is
+ * kept for later calls on the same contexts in the same order (dropped by
+ * eofa_set_system or eofa_destroy of any of them).  Each system's outer
+ * steps and inner iterations equal those of its eofa_solve.  With
+ * opts->kernel_timing, opts->precond or opts->method set the systems are
+ * solved one by one.  Contexts must be distinct. */
 eofa_status eofa_solve_batched(eofa_ctx *const *ctx, int n, const void *const *rhs,
                                void *const *sol, const eofa_solve_opts *opts,
                                eofa_solve_stats *stats, void *stream);

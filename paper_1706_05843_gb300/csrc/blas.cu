@@ -3,6 +3,7 @@
 // caller's canonical complex128 fields and the internal even-odd blocked
 // layout.  One thread per 5D site (xcb, s) of a half lattice.
 #include "blas.h"
+#include "eofa.h"
 #include "learned.h"
 
 namespace eofa {
@@ -56,58 +57,143 @@ cudaError_t while_cond(cudaGraphConditionalHandle h, DevScal* sc, cudaStream_t s
     return cudaGetLastError();
 }
 
-// Batched solves: the loop goes on while any system still iterates.
-__global__ void k_while_cond_all(cudaGraphConditionalHandle h, ScalList L) {
-    int go = 0;
-    for (int i = 0; i < L.n; ++i) {
-        const DevScal* sc = L.s[i];
-        if (!sc->done && !sc->nonfinite && sc->iters < sc->max_iters) go = 1;
-    }
-    cudaGraphSetConditional(h, go ? 1u : 0u);
+// ---------------------------------------------------------------------------
+// device-driven defect correction of a batched solve: each system runs the
+// outer FP64 loop on its own scalars.  In every chunk of the batch graph the
+// running systems take kChunk CG iterations; the gate then turns a system
+// whose inner solve has ended to its outer step (accumulate the correction,
+// FP64 residual, decide), which ends its outer loop or restarts the inner
+// CGNR at once.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool past_deadline(const DevScal* sc) {
+    return sc->o_timeout_ns && globaltimer_ns() - sc->o_t0_ns > sc->o_timeout_ns;
 }
 
-cudaError_t while_cond_all(cudaGraphConditionalHandle h, const ScalList& L, cudaStream_t st) {
-    k_while_cond_all<<<1, 1, 0, st>>>(h, L);
-    return cudaGetLastError();
+__device__ __forceinline__ void outer_end(DevScal* sc, int status) {
+    sc->o_fin = 1;
+    sc->o_status = status;
+    sc->o_skip_restart = 1;
+    sc->done = 1;
+    sc->stop = 1;
 }
 
-// Host-set control of a batched round: skip flag and iteration budget.
-__global__ void k_inner_ctl(DevScal* sc, int skip, int max_iters) {
-    sc->skip = skip;
-    sc->max_iters = max_iters;
-}
-
-cudaError_t inner_ctl(DevScal* sc, int skip, int max_iters, cudaStream_t st) {
-    k_inner_ctl<<<1, 1, 0, st>>>(sc, skip, max_iters);
-    return cudaGetLastError();
-}
-
-// Start of a batched inner solve, on the device: the outer residual
-// |r|^2 = store[0] and |b|^2 = store[1] + store[2] give the inner target
-// max(floor, tol |b| / |r|); a system that has converged (or skips) is
-// marked done and its kernels return at once.
-__global__ void k_inner_init(DevScal* sc, double tol, double floor_tol) {
-    const double rr = sc->store[0], bb = sc->store[1] + sc->store[2];
-    sc->qq = sc->zz = sc->rr = sc->alpha = sc->beta = 0.0;
+__global__ void k_outer_begin(DevScal* sc, double tol, double floor_tol, int maxit, int maxouter,
+                              unsigned long long timeout_ns, int fin, int x_zero, int body_cap) {
+    sc->tol = tol;
+    sc->floor_tol = floor_tol;
+    sc->maxit = maxit;
+    sc->maxouter = maxouter;
+    sc->o_t0_ns = globaltimer_ns();
+    sc->o_timeout_ns = timeout_ns;
+    sc->o_body = 0;
+    sc->o_body_cap = body_cap;
+    sc->outer = sc->total = 0;
+    sc->rel = fin ? 0.0 : 1.0;
+    sc->o_fin = fin;
+    sc->o_status = EOFA_OK;
+    sc->o_skip_copy = fin || !x_zero;
+    sc->o_skip_res = fin || x_zero;
+    sc->o_skip_step = 1;
+    sc->o_skip_restart = 1;
+    sc->done = sc->stop = 1;
     sc->iters = 0;
     sc->nonfinite = 0;
     sc->timed_out = 0;
     sc->timeout_ns = 0;
-    sc->t0_ns = globaltimer_ns();
-    const double rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
-    if (sc->skip || !(rel > tol)) {
-        sc->done = 1;
-        sc->stop = 1;
-        return;
-    }
-    const double t = fmax(tol / rel, floor_tol);
-    sc->target_rr = t * t;
-    sc->done = 0;
-    sc->stop = 0;
 }
 
-cudaError_t inner_init(DevScal* sc, double tol, double floor_tol, cudaStream_t st) {
-    k_inner_init<<<1, 1, 0, st>>>(sc, tol, floor_tol);
+cudaError_t outer_begin(DevScal* sc, double tol, double floor_tol, int maxit, int maxouter,
+                        unsigned long long timeout_ns, int fin, int x_zero, int body_cap, cudaStream_t st) {
+    k_outer_begin<<<1, 1, 0, st>>>(sc, tol, floor_tol, maxit, maxouter, timeout_ns, fin, x_zero, body_cap);
+    return cudaGetLastError();
+}
+
+// After a chunk: a running system whose inner solve has ended (done,
+// non-finite, out of iterations, or past the deadline) takes its outer step
+// in this chunk; its CG kernels return at once from here on.
+__global__ void k_outer_gate(DevScal* sc) {
+    sc->o_skip_step = 1;
+    if (sc->o_fin) return;
+    const bool timed = past_deadline(sc);
+    if (!(sc->done || sc->nonfinite || sc->iters >= sc->max_iters || timed)) return;
+    sc->total += sc->iters;
+    sc->outer += 1;
+    sc->done = sc->stop = 1;
+    if (sc->nonfinite) {
+        outer_end(sc, EOFA_ERR_NONFINITE);
+        return;
+    }
+    sc->o_skip_step = 0;
+}
+
+cudaError_t outer_gate(DevScal* sc, cudaStream_t st) {
+    k_outer_gate<<<1, 1, 0, st>>>(sc);
+    return cudaGetLastError();
+}
+
+// After an FP64 residual |r|^2 = store[0] (|b|^2 = store[1] + store[2]):
+// end the outer loop (non-finite, converged, iteration caps, deadline, in
+// that order) or restart the inner CGNR on r / |r| with the target
+// max(floor, tol |b| / |r|) and the iterations left.  first: the residual of
+// the loop's start (taken whether or not a step ran).
+__global__ void k_outer_decide(DevScal* sc, int first) {
+    if (sc->o_fin || (!first && sc->o_skip_step)) {
+        sc->o_skip_restart = 1;
+        return;
+    }
+    const double rr = sc->store[0], bb = sc->store[1] + sc->store[2];
+    if (!isfinite(rr)) {
+        outer_end(sc, EOFA_ERR_NONFINITE);
+        return;
+    }
+    const double rel = sqrt(rr / bb);
+    sc->rel = rel;
+    if (!(rel > sc->tol)) {
+        outer_end(sc, EOFA_OK);
+        return;
+    }
+    if (sc->outer >= sc->maxouter || sc->total >= sc->maxit) {
+        outer_end(sc, EOFA_ERR_NOT_CONVERGED);
+        return;
+    }
+    if (past_deadline(sc)) {
+        outer_end(sc, EOFA_ERR_TIMEOUT);
+        return;
+    }
+    const double t = fmax(sc->tol / rel, sc->floor_tol);
+    sc->target_rr = t * t;
+    sc->qq = sc->zz = sc->rr = sc->alpha = sc->beta = 0.0;
+    sc->iters = 0;
+    sc->nonfinite = 0;
+    sc->max_iters = sc->maxit - sc->total;
+    sc->done = sc->stop = 0;
+    sc->o_skip_restart = 0;
+}
+
+cudaError_t outer_decide_dev(DevScal* sc, int first, cudaStream_t st) {
+    k_outer_decide<<<1, 1, 0, st>>>(sc, first);
+    return cudaGetLastError();
+}
+
+// Condition of the batch graph's WHILE node: another chunk while any
+// system's outer loop runs.  The chunk count of system 0 is bounded; a batch
+// that reaches the bound ends its running systems as not converged.
+__global__ void k_outer_cond(cudaGraphConditionalHandle h, ScalList L) {
+    DevScal* s0 = L.s[0];
+    int go = 0;
+    for (int i = 0; i < L.n; ++i)
+        if (!L.s[i]->o_fin) go = 1;
+    s0->o_body += 1;
+    if (go && s0->o_body >= s0->o_body_cap) {
+        for (int i = 0; i < L.n; ++i)
+            if (!L.s[i]->o_fin) outer_end(L.s[i], EOFA_ERR_NOT_CONVERGED);
+        go = 0;
+    }
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+cudaError_t outer_cond(cudaGraphConditionalHandle h, const ScalList& L, cudaStream_t st) {
+    k_outer_cond<<<1, 1, 0, st>>>(h, L);
     return cudaGetLastError();
 }
 
@@ -176,9 +262,10 @@ __global__ void __launch_bounds__(BT) k_cg_px(VecRef x, VecRef p, VecRef z, long
 // Scale: a = scale, or 1/sqrt(store[slot]) when inv_sqrt_slot >= 0.
 template <typename SD, typename SS>
 __global__ void __launch_bounds__(BT) k_copy(VecRef dst, VecRef src, long n5, int Ls, double scale,
-                                             int inv_sqrt_slot, Reduce rd) {
+                                             int inv_sqrt_slot, Reduce rd, const int* skip) {
     typedef typename Traits<SD>::R RD;
     typedef typename Traits<SS>::R RS;
+    if (skip && *skip) return;
     const long t = (long)blockIdx.x * BT + threadIdx.x;
     RD nn = (RD)0;
     if (t < n5) {
@@ -205,8 +292,9 @@ __global__ void __launch_bounds__(BT) k_copy(VecRef dst, VecRef src, long n5, in
 // x (FP64) += sqrt(store[slot]) * e  (defect-correction update)
 template <typename SE>
 __global__ void __launch_bounds__(BT) k_acc(VecRef x, VecRef e, long n5, int Ls, const DevScal* sc,
-                                            int slot) {
+                                            int slot, const int* skip) {
     typedef typename Traits<SE>::R RE;
+    if (skip && *skip) return;
     const long t = (long)blockIdx.x * BT + threadIdx.x;
     if (t >= n5) return;
     const long xcb = t / Ls;
@@ -222,7 +310,9 @@ __global__ void __launch_bounds__(BT) k_acc(VecRef x, VecRef e, long n5, int Ls,
 }
 
 // r = b - q (FP64), |r|^2 reduced
-__global__ void __launch_bounds__(BT) k_sub(VecRef r, VecRef b, VecRef q, long n5, int Ls, Reduce rd) {
+__global__ void __launch_bounds__(BT) k_sub(VecRef r, VecRef b, VecRef q, long n5, int Ls, Reduce rd,
+                                            const int* skip) {
+    if (skip && *skip) return;
     const long t = (long)blockIdx.x * BT + threadIdx.x;
     double nn = 0.0;
     if (t < n5) {
@@ -242,8 +332,9 @@ __global__ void __launch_bounds__(BT) k_sub(VecRef r, VecRef b, VecRef q, long n
 }
 
 template <typename S>
-__global__ void __launch_bounds__(BT) k_zero(VecRef v, long n5, int Ls) {
+__global__ void __launch_bounds__(BT) k_zero(VecRef v, long n5, int Ls, const int* skip) {
     typedef typename Traits<S>::R R;
+    if (skip && *skip) return;
     const long t = (long)blockIdx.x * BT + threadIdx.x;
     if (t >= n5) return;
     const long xcb = t / Ls;
@@ -402,35 +493,36 @@ cudaError_t blas_cg_px(int prec, int xprec, VecRef x, VecRef p, VecRef z, long n
 }
 
 cudaError_t blas_copy(int dprec, VecRef dst, int sprec, VecRef src, long n5, int Ls, double scale,
-                      int inv_sqrt_slot, Reduce rd, cudaStream_t st) {
+                      int inv_sqrt_slot, Reduce rd, cudaStream_t st, const int* skip) {
     return dispatch_prec(dprec, [&](auto* dtag) -> cudaError_t {
         typedef std::remove_pointer_t<decltype(dtag)> SD;
         return dispatch_prec(sprec, [&](auto* stag) -> cudaError_t {
             typedef std::remove_pointer_t<decltype(stag)> SS;
-            k_copy<SD, SS><<<grid_for(n5), BT, 0, st>>>(dst, src, n5, Ls, scale, inv_sqrt_slot, rd);
+            k_copy<SD, SS><<<grid_for(n5), BT, 0, st>>>(dst, src, n5, Ls, scale, inv_sqrt_slot, rd, skip);
             return cudaGetLastError();
         });
     });
 }
 
 cudaError_t blas_acc(VecRef x, int eprec, VecRef e, long n5, int Ls, const DevScal* sc, int slot,
-                     cudaStream_t st) {
+                     cudaStream_t st, const int* skip) {
     return dispatch_prec(eprec, [&](auto* tag) -> cudaError_t {
         typedef std::remove_pointer_t<decltype(tag)> SE;
-        k_acc<SE><<<grid_for(n5), BT, 0, st>>>(x, e, n5, Ls, sc, slot);
+        k_acc<SE><<<grid_for(n5), BT, 0, st>>>(x, e, n5, Ls, sc, slot, skip);
         return cudaGetLastError();
     });
 }
 
-cudaError_t blas_sub(VecRef r, VecRef b, VecRef q, long n5, int Ls, Reduce rd, cudaStream_t st) {
-    k_sub<<<grid_for(n5), BT, 0, st>>>(r, b, q, n5, Ls, rd);
+cudaError_t blas_sub(VecRef r, VecRef b, VecRef q, long n5, int Ls, Reduce rd, cudaStream_t st,
+                     const int* skip) {
+    k_sub<<<grid_for(n5), BT, 0, st>>>(r, b, q, n5, Ls, rd, skip);
     return cudaGetLastError();
 }
 
-cudaError_t blas_zero(int prec, VecRef v, long n5, int Ls, cudaStream_t st) {
+cudaError_t blas_zero(int prec, VecRef v, long n5, int Ls, cudaStream_t st, const int* skip) {
     return dispatch_prec(prec, [&](auto* tag) -> cudaError_t {
         typedef std::remove_pointer_t<decltype(tag)> S;
-        k_zero<S><<<grid_for(n5), BT, 0, st>>>(v, n5, Ls);
+        k_zero<S><<<grid_for(n5), BT, 0, st>>>(v, n5, Ls, skip);
         return cudaGetLastError();
     });
 }

@@ -27,21 +27,26 @@ cudaError_t launch_hop_f32_outer(int kind, const HopArgs& a, const void* coef, c
 cudaError_t scal_init(DevScal* sc, double target_rr, int max_iters, unsigned long long timeout_ns,
                       cudaStream_t st);
 cudaError_t while_cond(cudaGraphConditionalHandle h, DevScal* sc, cudaStream_t st);
-cudaError_t while_cond_all(cudaGraphConditionalHandle h, const ScalList& L, cudaStream_t st);
-cudaError_t inner_ctl(DevScal* sc, int skip, int max_iters, cudaStream_t st);
-cudaError_t inner_init(DevScal* sc, double tol, double floor_tol, cudaStream_t st);
+// device-driven defect correction of a batched solve (blas.cu)
+cudaError_t outer_begin(DevScal* sc, double tol, double floor_tol, int maxit, int maxouter,
+                        unsigned long long timeout_ns, int fin, int x_zero, int body_cap, cudaStream_t st);
+cudaError_t outer_gate(DevScal* sc, cudaStream_t st);
+cudaError_t outer_decide_dev(DevScal* sc, int first, cudaStream_t st);
+cudaError_t outer_cond(cudaGraphConditionalHandle h, const ScalList& L, cudaStream_t st);
 // r -= alpha q with |r|^2 (rd: FIN_RR); returns at once when *done
 cudaError_t blas_cg_r(int prec, VecRef q, VecRef r, long n5, int Ls, Reduce rd, const int* done,
                       cudaStream_t st);
 // x += alpha p; p = z + beta p unless done (rd: FIN_STOP on the same scalars)
 cudaError_t blas_cg_px(int prec, int xprec, VecRef x, VecRef p, VecRef z, long n5, int Ls, Reduce rd,
                        cudaStream_t st);
+// skip (may be NULL): the kernel returns at once while *skip is nonzero
 cudaError_t blas_copy(int dprec, VecRef dst, int sprec, VecRef src, long n5, int Ls, double scale,
-                      int inv_sqrt_slot, Reduce rd, cudaStream_t st);
+                      int inv_sqrt_slot, Reduce rd, cudaStream_t st, const int* skip = nullptr);
 cudaError_t blas_acc(VecRef x, int eprec, VecRef e, long n5, int Ls, const DevScal* sc, int slot,
-                     cudaStream_t st);
-cudaError_t blas_sub(VecRef r, VecRef b, VecRef q, long n5, int Ls, Reduce rd, cudaStream_t st);
-cudaError_t blas_zero(int prec, VecRef v, long n5, int Ls, cudaStream_t st);
+                     cudaStream_t st, const int* skip = nullptr);
+cudaError_t blas_sub(VecRef r, VecRef b, VecRef q, long n5, int Ls, Reduce rd, cudaStream_t st,
+                     const int* skip = nullptr);
+cudaError_t blas_zero(int prec, VecRef v, long n5, int Ls, cudaStream_t st, const int* skip = nullptr);
 cudaError_t layout_import(VecRef dst, const double* src, const Geom& g, int par, int g5r5, cudaStream_t st);
 cudaError_t layout_export(double* dst, VecRef src, const Geom& g, int par, int g5r5, cudaStream_t st);
 cudaError_t gauge_import(const double* U, const Geom& g, void* const links[4][2], int* bad, cudaStream_t st);

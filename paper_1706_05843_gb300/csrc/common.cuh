@@ -75,8 +75,22 @@ struct DevScal {
     unsigned long long t0_ns;      // %globaltimer at the start of the solve
     unsigned long long timeout_ns; // 0: none
     int timed_out;
-    int skip;                      // batched solves: this system sits the round out
     int stop;                      // the CG update of x and p has run after done was set
+    // device-driven defect correction of a batched solve (one graph launch):
+    // every flag below is read by the kernels of one phase, which return at
+    // once while it is nonzero
+    int o_fin;           // the outer loop of this system has ended (status in o_status)
+    int o_status;        // eofa_status of the ended outer loop
+    int o_skip_copy;     // first residual is the source itself (no initial guess) unless set
+    int o_skip_res;      // first residual is b~o - S x_o (initial guess) unless set
+    int o_skip_step;     // no outer step (accumulate, FP64 residual, decide) in this chunk
+    int o_skip_restart;  // no inner restart in this chunk
+    int outer, total;    // outer steps taken, inner iterations summed over them
+    int maxouter, maxit;
+    int o_body;          // chunks run (system 0 of a batch counts for the batch)
+    int o_body_cap;      // safety bound on the chunks (never reached by a sound solve)
+    double tol, floor_tol, rel;
+    unsigned long long o_t0_ns, o_timeout_ns;
 };
 
 // the device scalars of up to 32 systems (one batched graph)

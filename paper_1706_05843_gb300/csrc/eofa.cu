@@ -10,6 +10,8 @@
 //   x_e = K_ee^-1 (b_e - K_eo x_o)                     reconstruction
 //   psi = D~(m1) psi'                                  undo the Cayley form
 //   true residual ||b - K psi'|| / ||b|| in FP64
+#include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -95,6 +97,7 @@ struct eofa_ctx {
     // allocated on first use; multi-dot partial sums and results
     std::vector<double*> act5;
     double* mdot = nullptr;
+    unsigned long long uid = 0;  // identity of the context for the kept batch graphs
 };
 
 namespace {
@@ -499,19 +502,20 @@ eofa_status cg_iteration(eofa_ctx* c, int P, cudaStream_t st, bool timed, cudaEv
 }
 
 // Start of an inner CGNR from x = 0 on the source in inner.r (scal already
-// initialised): z = S^dag r (|z|^2 -> zz), p = z.
-eofa_status cg_start(eofa_ctx* c, int P, const int* done, cudaStream_t st) {
+// initialised): z = S^dag r (|z|^2 -> zz), p = z.  skip (may be NULL): every
+// kernel returns at once while *skip is nonzero.
+eofa_status cg_start(eofa_ctx* c, int P, const int* skip, cudaStream_t st) {
     Inner& in = c->inner[P];
     const int xp = P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
     const VecRef none{};
     eofa_status s;
     const bool dn = c->method == 1;
-    CKL(blas_zero(xp, in.x, c->n5, c->g.Ls, st), "blas_zero");
-    if ((s = hop(c, P, dn ? KIND_D_EO_DAG : KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), done, st)))
+    CKL(blas_zero(xp, in.x, c->n5, c->g.Ls, st, skip), "blas_zero");
+    if ((s = hop(c, P, dn ? KIND_D_EO_DAG : KIND_EO_MINV_DAG, 0, in.r, none, in.t, red(c, FIN_NONE), skip, st)))
         return s;
-    if ((s = hop(c, P, dn ? KIND_D_OE_DAG : KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_ZZ), done, st)))
+    if ((s = hop(c, P, dn ? KIND_D_OE_DAG : KIND_OE_SCHUR_DAG, 1, in.t, in.r, in.z, red(c, FIN_ZZ), skip, st)))
         return s;
-    CKL(blas_copy(P, in.p, P, in.z, c->n5, c->g.Ls, 1.0, -1, red(c, FIN_NONE), st), "blas_copy");
+    CKL(blas_copy(P, in.p, P, in.z, c->n5, c->g.Ls, 1.0, -1, red(c, FIN_NONE), st, skip), "blas_copy");
     return EOFA_OK;
 }
 
@@ -998,17 +1002,61 @@ eofa_status solve_impl(eofa_ctx* c, const double* rhs, double* sol, const eofa_s
 }
 
 // ---------------------------------------------------------------------------
-// batched solves: one CUDA graph per call holds, for every system, the
-// inner-solve prologue (parallel branches) and then a device-driven WHILE
-// node whose body runs kChunk CG iterations of every system (again parallel
-// branches) and a condition kernel over all systems.  Systems of different
-// lattices and Ls run side by side; converged systems turn into empty
-// kernels.  The host only runs the outer FP64 defect-correction step.
+// batched solves: the whole FP64 defect correction of every system is one
+// CUDA graph launch.  The graph holds, per system (parallel branches), the
+// first FP64 residual and the first inner start, then a WHILE node whose
+// body runs kChunk CG iterations of every system and, per system, the gate,
+// the outer step (x += |r| e, FP64 residual r = b~o - S x_o) and the
+// decision, which ends the system's outer loop or restarts its inner CGNR;
+// a condition kernel over all systems closes the body.  Each phase's kernels
+// return at once unless the system's device flags select them, so systems of
+// different lattices, Ls and iteration counts advance independently.  The
+// graph bakes in only context-owned buffers and is kept for later calls on
+// the same contexts.
 // ---------------------------------------------------------------------------
 constexpr int kBatchMax = 32;
 
-eofa_status build_batch_graph(eofa_ctx* const* cs, int n, int P, double tol, double floor_tol,
-                              cudaGraphExec_t* exec_out) {
+std::atomic<unsigned long long> g_ctx_uid{0};
+
+struct BatchGraph {
+    std::vector<unsigned long long> uids;
+    int P = 0;
+    cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_batch_mu;
+std::vector<BatchGraph> g_batch_graphs;  // least recently used first
+constexpr size_t kBatchGraphsKept = 4;
+
+// Drop the kept batch graphs that involve a context (its operator changed
+// or it is being destroyed).
+void drop_batch_graphs(unsigned long long uid) {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    for (size_t i = 0; i < g_batch_graphs.size();) {
+        const auto& u = g_batch_graphs[i].uids;
+        if (std::find(u.begin(), u.end(), uid) != u.end()) {
+            cudaGraphExecDestroy(g_batch_graphs[i].exec);
+            g_batch_graphs.erase(g_batch_graphs.begin() + (long)i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+// kernels of one system in one chunk of the batch graph (outer gate, step,
+// decision and restart included), and of the first residual and start
+constexpr int kBatchBodyKernels = 6 * kChunk + 11;
+constexpr int kBatchStartKernels = 10;
+
+// The outer step and the inner restart of system c in precision P: each
+// kernel is gated by its device flag.
+eofa_status batch_restart(eofa_ctx* c, int P, cudaStream_t st) {
+    Inner& in = c->inner[P];
+    const int* rs = &c->scal->o_skip_restart;
+    CKL(blas_copy(P, in.r, 0, c->ro, c->n5, c->g.Ls, 1.0, 0, red(c, FIN_NONE), st, rs), "copy");
+    return cg_start(c, P, rs, st);
+}
+
+eofa_status build_batch_graph(eofa_ctx* const* cs, int n, int P, cudaGraphExec_t* exec_out) {
     eofa_ctx* c = cs[0];  // errors are reported on the first context
     std::vector<cudaStream_t> str(n + 1, nullptr);
     std::vector<cudaEvent_t> evs(n + 1, nullptr);
@@ -1041,20 +1089,30 @@ eofa_status build_batch_graph(eofa_ctx* const* cs, int n, int P, double tol, dou
         }
         return ee == cudaSuccess ? EOFA_OK : cuda_fail(c, ee, "join");
     };
-    // prologue graph
+    const VecRef none{};
+    // first residual: r = b~o (no initial guess) or b~o - S x_o, then the
+    // decision and the first inner start
     e = cudaStreamBeginCapture(str[n], cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "capture"); }
     s = capture_branches([&](int i, cudaStream_t st) -> eofa_status {
         eofa_ctx* ci = cs[i];
-        Inner& in = ci->inner[P];
-        CK(inner_init(ci->scal, tol, floor_tol, st), "inner_init");
-        CK(blas_copy(P, in.r, 0, ci->ro, ci->n5, ci->g.Ls, 1.0, 0, red(ci, FIN_NONE), st), "copy");
-        return cg_start(ci, P, &ci->scal->done, st);
+        DevScal* sc = ci->scal;
+        eofa_status r;
+        eofa_ctx* c = ci;  // CK/CKL report on this system
+        CKL(blas_copy(0, ci->ro, 0, ci->bto, ci->n5, ci->g.Ls, 1.0, -1, red(ci, FIN_STORE, 0), st,
+                      &sc->o_skip_copy), "copy");
+        if ((r = hop(ci, 0, KIND_EO_MINV, 0, ci->x[1], none, ci->t[0], red(ci, FIN_NONE), &sc->o_skip_res, st)))
+            return r;
+        if ((r = hop(ci, 0, KIND_OE_SCHUR, 1, ci->t[0], ci->x[1], ci->qo, red(ci, FIN_NONE), &sc->o_skip_res, st)))
+            return r;
+        CKL(blas_sub(ci->ro, ci->bto, ci->qo, ci->n5, ci->g.Ls, red(ci, FIN_STORE, 0), st, &sc->o_skip_res), "sub");
+        CKL(outer_decide_dev(sc, 1, st), "outer_decide");
+        return batch_restart(ci, P, st);
     });
     cudaError_t e2 = cudaStreamEndCapture(str[n], &pro);
     if (s == EOFA_OK && e2 != cudaSuccess) s = cuda_fail(c, e2, "end capture");
     if (s != EOFA_OK) { cleanup(); return s; }
-    // top graph: prologue (child graph) -> WHILE
+    // top graph: first residual and start (child graph) -> WHILE
     cudaGraphNode_t child, wn;
     e = cudaGraphCreate(&g, 0);
     if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&child, g, nullptr, 0, pro);
@@ -1072,18 +1130,30 @@ eofa_status build_batch_graph(eofa_ctx* const* cs, int n, int P, double tol, dou
     cudaGraph_t body = np.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(str[n], body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cleanup(); return cuda_fail(c, e, "capture body"); }
+    const int xp = P == EOFA_F64 ? EOFA_F64 : EOFA_F32;
     s = capture_branches([&](int i, cudaStream_t st) -> eofa_status {
+        eofa_ctx* ci = cs[i];
+        DevScal* sc = ci->scal;
+        eofa_ctx* c = ci;
         eofa_status r = EOFA_OK;
-        for (int k = 0; k < kChunk && r == EOFA_OK; ++k) r = cg_iteration(cs[i], P, st, false);
-        return r;
+        for (int k = 0; k < kChunk && r == EOFA_OK; ++k) r = cg_iteration(ci, P, st, false);
+        if (r != EOFA_OK) return r;
+        CKL(outer_gate(sc, st), "outer_gate");
+        const int* os = &sc->o_skip_step;
+        CKL(blas_acc(ci->x[1], xp, ci->inner[P].x, ci->n5, ci->g.Ls, sc, 0, st, os), "acc");
+        if ((r = hop(ci, 0, KIND_EO_MINV, 0, ci->x[1], none, ci->t[0], red(ci, FIN_NONE), os, st))) return r;
+        if ((r = hop(ci, 0, KIND_OE_SCHUR, 1, ci->t[0], ci->x[1], ci->qo, red(ci, FIN_NONE), os, st))) return r;
+        CKL(blas_sub(ci->ro, ci->bto, ci->qo, ci->n5, ci->g.Ls, red(ci, FIN_STORE, 0), st, os), "sub");
+        CKL(outer_decide_dev(sc, 0, st), "outer_decide");
+        return batch_restart(ci, P, st);
     });
     if (s == EOFA_OK) {
         ScalList L;
         std::memset(&L, 0, sizeof(L));
         L.n = n;
         for (int i = 0; i < n; ++i) L.s[i] = cs[i]->scal;
-        e = while_cond_all(h, L, str[n]);
-        if (e != cudaSuccess) s = cuda_fail(c, e, "while_cond_all");
+        e = outer_cond(h, L, str[n]);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "outer_cond");
     }
     cudaGraph_t cap = nullptr;
     e2 = cudaStreamEndCapture(str[n], &cap);
@@ -1094,6 +1164,38 @@ eofa_status build_batch_graph(eofa_ctx* const* cs, int n, int P, double tol, dou
     }
     cleanup();
     return s;
+}
+
+// The kept graph of these contexts in precision P, built on first use.
+eofa_status batch_graph(eofa_ctx* const* cs, int n, int P, cudaGraphExec_t* exec) {
+    std::vector<unsigned long long> uids(n);
+    for (int i = 0; i < n; ++i) uids[i] = cs[i]->uid;
+    {
+        std::lock_guard<std::mutex> lock(g_batch_mu);
+        for (size_t i = 0; i < g_batch_graphs.size(); ++i)
+            if (g_batch_graphs[i].P == P && g_batch_graphs[i].uids == uids) {
+                BatchGraph b = g_batch_graphs[i];
+                g_batch_graphs.erase(g_batch_graphs.begin() + (long)i);
+                g_batch_graphs.push_back(b);
+                *exec = b.exec;
+                return EOFA_OK;
+            }
+    }
+    cudaGraphExec_t x = nullptr;
+    eofa_status s = build_batch_graph(cs, n, P, &x);
+    if (s != EOFA_OK) return s;
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    if (g_batch_graphs.size() >= kBatchGraphsKept) {
+        cudaGraphExecDestroy(g_batch_graphs.front().exec);
+        g_batch_graphs.erase(g_batch_graphs.begin());
+    }
+    BatchGraph b;
+    b.uids = uids;
+    b.P = P;
+    b.exec = x;
+    g_batch_graphs.push_back(b);
+    *exec = x;
+    return EOFA_OK;
 }
 
 eofa_status solve_batched_impl(eofa_ctx* const* cs, int n, const void* const* rhs, void* const* sol,
@@ -1114,54 +1216,50 @@ eofa_status solve_batched_impl(eofa_ctx* const* cs, int n, const void* const* rh
     for (int i = 0; i < n; ++i)
         if ((s = solve_check_rhs(cs[i], (double*)sol[i], ss[i], st))) return s;
     const int P = ss[0].P;
+    std::vector<long> launches0(n);
+    for (int i = 0; i < n; ++i) launches0[i] = cs[i]->launches;
     cudaGraphExec_t exec = nullptr;
-    if ((s = build_batch_graph(cs, n, P, o.tol, inner_tol_floor(o, P), &exec))) return s;
-    for (;;) {
-        int active = 0;
-        for (int i = 0; i < n; ++i)
-            if (!ss[i].finished && (s = outer_residual(cs[i], ss[i], st))) { cudaGraphExecDestroy(exec); return s; }
-        if (const cudaError_t e = cudaStreamSynchronize(st); e != cudaSuccess) {
-            cudaGraphExecDestroy(exec);
-            return cuda_fail(cs[0], e, "batched outer residual");
+    s = batch_graph(cs, n, P, &exec);
+    for (int i = 0; i < n; ++i) cs[i]->launches = launches0[i];  // the capture launched nothing
+    if (s != EOFA_OK) return s;
+    // every system's options, deadline and first-residual form, then the
+    // one launch of the whole defect correction
+    const int body_cap = ss[0].maxit / kChunk + ss[0].maxouter + 4;
+    for (int i = 0; i < n; ++i) {
+        eofa_ctx* c = cs[i];
+        unsigned long long tns = 0;
+        if (o.timeout_ms > 0) {
+            const double left_ms = (double)o.timeout_ms - since(ss[i].t0) * 1e3;
+            tns = left_ms > 1e-6 ? (unsigned long long)(left_ms * 1e6) : 1ull;
         }
-        for (int i = 0; i < n; ++i) {
-            if (ss[i].finished) continue;
-            if (!outer_decide(cs[i], o, ss[i])) ss[i].finished = true;
-            else ++active;
-        }
-        // every system gets its skip flag and iteration budget for this round
-        for (int i = 0; i < n; ++i) {
-            eofa_ctx* c = cs[i];
-            CKL(inner_ctl(c->scal, ss[i].finished ? 1 : 0, std::max(1, ss[i].maxit - ss[i].total), st), "inner_ctl");
-        }
-        if (active == 0) break;
-        if (const cudaError_t e = cudaGraphLaunch(exec, st); e != cudaSuccess) {
-            cudaGraphExecDestroy(exec);
-            return cuda_fail(cs[0], e, "batched graph launch");
-        }
-        for (int i = 0; i < n; ++i)
-            if ((s = enqueue_read(cs[i], st))) { cudaGraphExecDestroy(exec); return s; }
-        if (const cudaError_t e = cudaStreamSynchronize(st); e != cudaSuccess) {
-            cudaGraphExecDestroy(exec);
-            return cuda_fail(cs[0], e, "batched inner solves");
-        }
-        for (int i = 0; i < n; ++i) {
-            if (ss[i].finished) continue;
-            eofa_ctx* c = cs[i];
-            const DevScal& h = *c->h_scal;
-            ss[i].total += h.iters;
-            ++ss[i].outer;
-            c->launches += (long)(6 * kChunk) * ((h.iters + kChunk - 1) / kChunk + (h.iters == 0 ? 1 : 0));
-            if (h.nonfinite) {
-                ss[i].result = fail(c, EOFA_ERR_NONFINITE, "NaN or Inf in the inner CG reductions");
-                ss[i].finished = true;
-                continue;
-            }
-            CKL(blas_acc(c->x[1], ss[i].xp, c->inner[P].x, c->n5, c->g.Ls, c->scal, 0, st), "acc");
-            ss[i].x_zero = false;
+        CKL(outer_begin(c->scal, o.tol, inner_tol_floor(o, P), ss[i].maxit, ss[i].maxouter, tns,
+                        ss[i].finished ? 1 : 0, ss[i].x_zero ? 1 : 0, body_cap, st), "outer_begin");
+    }
+    if (const cudaError_t e = cudaGraphLaunch(exec, st); e != cudaSuccess)
+        return cuda_fail(cs[0], e, "batched graph launch");
+    for (int i = 0; i < n; ++i)
+        if ((s = enqueue_read(cs[i], st))) return s;
+    if (const cudaError_t e = cudaStreamSynchronize(st); e != cudaSuccess)
+        return cuda_fail(cs[0], e, "batched solve");
+    const int chunks = cs[0]->h_scal->o_body;
+    for (int i = 0; i < n; ++i) {
+        eofa_ctx* c = cs[i];
+        const DevScal& h = *c->h_scal;
+        c->launches += kBatchStartKernels + (long)kBatchBodyKernels * chunks + (i == 0 ? chunks : 0);
+        if (ss[i].finished) continue;  // zero right-hand side
+        ss[i].outer = h.outer;
+        ss[i].total = h.total;
+        ss[i].rel = h.rel;
+        ss[i].finished = true;
+        switch (h.o_status) {
+            case EOFA_OK: ss[i].result = EOFA_OK; break;
+            case EOFA_ERR_NONFINITE:
+                ss[i].result = fail(c, EOFA_ERR_NONFINITE, "NaN or Inf in the defect correction");
+                break;
+            case EOFA_ERR_TIMEOUT: ss[i].result = fail(c, EOFA_ERR_TIMEOUT, "solve exceeded timeout_ms"); break;
+            default: ss[i].result = fail(c, EOFA_ERR_NOT_CONVERGED, "iteration cap"); break;
         }
     }
-    cudaGraphExecDestroy(exec);
     eofa_status first = EOFA_OK;
     for (int i = 0; i < n; ++i) {
         s = solve_end(cs[i], (double*)sol[i], o, ss[i], stats ? stats + i : nullptr, st);
@@ -1224,6 +1322,7 @@ void drop_graphs(eofa_ctx* c) {
             if (c->cg_first[m][i]) cudaGraphExecDestroy(c->cg_first[m][i]);
             c->cg_exec[m][i] = c->cg_first[m][i] = nullptr;
         }
+    drop_batch_graphs(c->uid);
 }
 
 // Make the context solve H(mh) + beta Delta_pm(ma, mb) P_pm on its lattice
@@ -1533,6 +1632,7 @@ static eofa_status create_impl(const eofa_params* p, const void* gauge, int gpma
     if (p->Ls != 4 && p->Ls != 8 && p->Ls != 12 && p->Ls != 16) return EOFA_ERR_UNSUPPORTED;
     eofa_ctx* c = new (std::nothrow) eofa_ctx();
     if (!c) return EOFA_ERR_OOM;
+    c->uid = ++g_ctx_uid;
     c->p = *p;
     Geom& g = c->g;
     g.X = p->dims[0]; g.Y = p->dims[1]; g.Z = p->dims[2];
@@ -1814,6 +1914,7 @@ eofa_status eofa_solve_batched(eofa_ctx* const* ctx, int n, const void* const* r
 
 void eofa_destroy(eofa_ctx* ctx) {
     if (!ctx) return;
+    drop_batch_graphs(ctx->uid);
     for (void* p : ctx->allocs) cudaFree(p);
     for (cudaEvent_t e : ctx->evs) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->nev)
