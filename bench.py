@@ -329,8 +329,9 @@ def run_learned(B, I, torch, dev):
     16^3x32 Ls=16 solves (gauge seed 3; a further 200 pairs held out to
     measure the trained network's error on unseen pairs), used in flexible
     GCR at 32^3x64 Ls=12 (FP32 inner, FP64 correction to 1e-10), against
-    plain CGNR and the untrained network; the convolution's tensor-core rate
-    from the forward passes of one application."""
+    plain CGNR, the untrained network and plain FP64 CG (estimated from two
+    capped FP64 solves); the convolution's tensor-core rate from the forward
+    passes of one application."""
     act = dict(WORKLOAD["action"])
     rng = np.random.default_rng(17)
     w0 = np.concatenate([rng.standard_normal(81 * co * ci) * np.sqrt(2.0 / (81 * ci))
@@ -355,6 +356,20 @@ def run_learned(B, I, torch, dev):
     s.solve(rhs, out=sol, tol=TOL, inner="f32")
     dt, (_, st) = _timed(torch, lambda: s.solve(rhs, out=sol, tol=TOL, inner="f32"))
     res["cgnr"] = {"s": dt, "inner_iters": st.inner_iters, "true_res": st.true_res}
+    # plain FP64 CG on the same system (about 80 s in full): two capped FP64
+    # solves give the time per iteration and the fixed cost (source,
+    # reconstruction, true residual); the estimate takes the mixed solve's
+    # iteration count (the FP64 and FP32-inner solves of the 16^3x32 workload
+    # take 632 and 638 iterations)
+    s.solve(rhs, out=sol, tol=TOL, inner="f64", max_iter=16, max_outer=1, check=False)  # tunes the FP64 kinds
+    t_lo, (_, s_lo) = _timed(torch, lambda: s.solve(rhs, out=sol, tol=TOL, inner="f64", max_iter=16, max_outer=1,
+                                                    check=False))
+    t_hi, (_, s_hi) = _timed(torch, lambda: s.solve(rhs, out=sol, tol=TOL, inner="f64", max_iter=64, max_outer=1,
+                                                    check=False))
+    per_it = (t_hi - t_lo) / max(1, s_hi.inner_iters - s_lo.inner_iters)
+    fixed = max(0.0, t_lo - per_it * s_lo.inner_iters)
+    res["fp64_cg_estimate"] = {"s": fixed + per_it * st.inner_iters, "s_per_iter": per_it, "s_fixed": fixed,
+                               "iters": st.inner_iters, "timed_iters": [s_lo.inner_iters, s_hi.inner_iters]}
     for name, weights in [("trained", w), ("untrained", w0)]:
         B.eofa_set_preconditioner(s.ctx, weights)
         dt, (_, st) = _timed(torch, lambda: s.solve(rhs, out=sol, tol=TOL, inner="f32", precond=1))
@@ -369,6 +384,7 @@ def run_learned(B, I, torch, dev):
             tf = flops * st.precond_iters / (st.precond_ms * 1e-3) / 1e12
             res[name]["net_tflops"] = tf
             res[name]["net_frac_of_bf16_sustained"] = tf / bf16_peaks()[1]
+        res[name]["speedup_vs_fp64_cg"] = res["fp64_cg_estimate"]["s"] / dt
     s.close()
     return res
 
