@@ -178,18 +178,21 @@ eofa_status eofa_solve(eofa_ctx *ctx, const void *rhs, void *sol,
 
 /* eofa_solve with the right-hand side and the solution in HOST memory
  * (complex128, same layout), on `stream`; returns when the solution is in
- * `sol`.  When both buffers are page-locked (cudaHostAlloc,
- * cudaHostRegister, torch pin_memory) the solver's import and export kernels
- * read rhs and write sol in place through their device mapping (over
- * NVLink-C2C on a Grace-Blackwell node), with no staging copies.  Otherwise
- * the call copies rhs to the device, solves and copies the solution back,
- * through two 5D work fields that the context allocates on first use and
- * keeps (the same ones the action calls use).  With opts->use_guess, sol
- * holds the initial guess on entry.  On the staging path the solution is
- * copied back for every status the solver itself returns (EOFA_OK,
- * EOFA_ERR_NOT_CONVERGED, EOFA_ERR_TIMEOUT, EOFA_ERR_NONFINITE) and argument
- * and CUDA errors leave sol untouched.  End-to-end entry of the solve as
- * Sec. V.A describes it (the paper has no separate host form). */
+ * `sol`.  A page-locked rhs (cudaHostAlloc, cudaHostRegister, torch
+ * pin_memory) is read in place by the solver's import kernels through its
+ * device mapping (over NVLink-C2C on a Grace-Blackwell node); a pageable one
+ * is copied to a device work field first.  The solution is exported to a
+ * device work field; into a page-locked sol it is copied by the copy engine
+ * on a second stream of the context while the FP64 true residual is
+ * computed, into a pageable sol after the solve.  The two 5D work fields are
+ * allocated by the context on first use and kept (the same ones the action
+ * calls use).  With opts->use_guess, sol holds the initial guess on entry
+ * (read in place when page-locked).  sol is written whenever the solver has
+ * produced a solution (EOFA_OK, EOFA_ERR_NOT_CONVERGED, EOFA_ERR_TIMEOUT,
+ * and EOFA_ERR_NONFINITE met in the iterations); argument errors, a
+ * non-finite right-hand side and CUDA errors leave it untouched.
+ * End-to-end entry of the solve as Sec. V.A describes it (the paper has no
+ * separate host form). */
 eofa_status eofa_solve_host(eofa_ctx *ctx, const double *rhs, double *sol,
                             const eofa_solve_opts *opts, eofa_solve_stats *stats,
                             void *stream);

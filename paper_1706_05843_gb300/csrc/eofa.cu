@@ -98,6 +98,11 @@ struct eofa_ctx {
     std::vector<double*> act5;
     double* mdot = nullptr;
     unsigned long long uid = 0;  // identity of the context for the kept batch graphs
+    // host-buffer solves: the solution's copy to page-locked host memory runs
+    // on this stream while the true residual is computed
+    cudaStream_t side = nullptr;
+    cudaEvent_t xev[2] = {};
+    bool exported = false;  // the current solve has written its solution
 };
 
 namespace {
@@ -807,6 +812,7 @@ eofa_status ensure_dense(eofa_ctx* c, cudaStream_t st) {
 eofa_status solve_begin(eofa_ctx* c, const double* rhs, const double* sol, const eofa_solve_opts& o,
                         SolveState& ss, cudaStream_t st) {
     ss.t0 = Clock::now();
+    c->exported = false;
     ss.P = o.inner;
     if (ss.P < 0 || ss.P > 3) return fail(c, EOFA_ERR_ARG, "opts.inner must be an eofa_prec");
     if (!(o.tol > 0.0)) return fail(c, EOFA_ERR_ARG, "opts.tol must be positive");
@@ -913,22 +919,28 @@ double inner_tol_floor(const eofa_solve_opts& o, int P) {
 
 // Phase 3: x_e = M^-1 (b_e + 1/2 D_h D~ x_o), the FP64 true residual of the
 // full system, psi = D~ psi' (H form), export and statistics.
+// host_sol (page-locked, may be NULL): the exported solution is copied there
+// on the context's side stream, overlapping the true residual.
 eofa_status solve_end(eofa_ctx* c, double* sol, const eofa_solve_opts& o, SolveState& ss,
-                      eofa_solve_stats* stats, cudaStream_t st) {
+                      eofa_solve_stats* stats, cudaStream_t st, double* host_sol = nullptr) {
     eofa_solve_stats S;
     std::memset(&S, 0, sizeof(S));
     const VecRef none{};
     const Geom& g = c->g;
     const int Ls = g.Ls;
+    const size_t bytes = (size_t)c->n5 * 2 * 24 * sizeof(double);
     eofa_status s;
+    if (host_sol && !c->side) {
+        CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "cudaStreamCreate");
+        for (auto& e : c->xev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+    }
     if (ss.bb == 0.0) {
+        if (host_sol) CK(cudaMemcpyAsync(host_sol, sol, bytes, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
         CK(cudaStreamSynchronize(st), "sync");
+        c->exported = true;
     } else {
         if ((s = hop(c, 0, KIND_RECON, 0, c->x[1], c->b[0], c->x[0], red(c, FIN_NONE), nullptr, st))) return s;
-        if ((s = hop(c, 0, KIND_FULL, 0, c->x[1], c->x[0], c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
-        if ((s = hop(c, 0, KIND_FULL, 1, c->x[0], c->x[1], c->t[1], red(c, FIN_NONE), nullptr, st))) return s;
-        CKL(blas_sub(c->t[0], c->b[0], c->t[0], c->n5, Ls, red(c, FIN_STORE, 3), st), "sub");
-        CKL(blas_sub(c->t[1], c->b[1], c->t[1], c->n5, Ls, red(c, FIN_STORE, 4), st), "sub");
+        // the solution first: psi = D~ psi' (H form) or psi' (K form)
         if (ss.H) {
             if ((s = hop(c, 0, KIND_LOC_DT, 0, none, c->x[0], c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
             if ((s = hop(c, 0, KIND_LOC_DT, 1, none, c->x[1], c->t[1], red(c, FIN_NONE), nullptr, st))) return s;
@@ -938,6 +950,19 @@ eofa_status solve_end(eofa_ctx* c, double* sol, const eofa_solve_opts& o, SolveS
             CKL(layout_export(sol, c->x[0], g, 0, 0, st), "export");
             CKL(layout_export(sol, c->x[1], g, 1, 0, st), "export");
         }
+        c->exported = true;
+        if (host_sol) {
+            CK(cudaEventRecord(c->xev[0], st), "cudaEventRecord");
+            CK(cudaStreamWaitEvent(c->side, c->xev[0], 0), "cudaStreamWaitEvent");
+            CK(cudaMemcpyAsync(host_sol, sol, bytes, cudaMemcpyDeviceToHost, c->side), "cudaMemcpyAsync");
+            CK(cudaEventRecord(c->xev[1], c->side), "cudaEventRecord");
+        }
+        // then the FP64 true residual of the full system
+        if ((s = hop(c, 0, KIND_FULL, 0, c->x[1], c->x[0], c->t[0], red(c, FIN_NONE), nullptr, st))) return s;
+        if ((s = hop(c, 0, KIND_FULL, 1, c->x[0], c->x[1], c->t[1], red(c, FIN_NONE), nullptr, st))) return s;
+        CKL(blas_sub(c->t[0], c->b[0], c->t[0], c->n5, Ls, red(c, FIN_STORE, 3), st), "sub");
+        CKL(blas_sub(c->t[1], c->b[1], c->t[1], c->n5, Ls, red(c, FIN_STORE, 4), st), "sub");
+        if (host_sol) CK(cudaStreamWaitEvent(st, c->xev[1], 0), "cudaStreamWaitEvent");
         if ((s = read_scal(c, st))) return s;
         S.true_res = std::sqrt((c->h_scal->store[3] + c->h_scal->store[4]) / ss.bb);
     }
@@ -960,11 +985,14 @@ eofa_status solve_end(eofa_ctx* c, double* sol, const eofa_solve_opts& o, SolveS
     return result;
 }
 
+// host_sol: see solve_end; guess (may be NULL): where the initial guess is
+// read instead of sol.
 eofa_status solve_impl(eofa_ctx* c, const double* rhs, double* sol, const eofa_solve_opts& o,
-                       eofa_solve_stats* stats, cudaStream_t st) {
+                       eofa_solve_stats* stats, cudaStream_t st, double* host_sol = nullptr,
+                       const double* guess = nullptr) {
     SolveState ss;
     eofa_status s;
-    if ((s = solve_begin(c, rhs, sol, o, ss, st))) return s;
+    if ((s = solve_begin(c, rhs, guess ? guess : sol, o, ss, st))) return s;
     CK(cudaStreamSynchronize(st), "sync");
     if ((s = solve_check_rhs(c, sol, ss, st))) return s;
     const int Ls = c->g.Ls;
@@ -998,7 +1026,7 @@ eofa_status solve_impl(eofa_ctx* c, const double* rhs, double* sol, const eofa_s
         CKL(blas_acc(c->x[1], ss.xp, e, c->n5, Ls, c->scal, 0, st), "acc");
         ss.x_zero = false;
     }
-    return solve_end(c, sol, o, ss, stats, st);
+    return solve_end(c, sol, o, ss, stats, st, host_sol);
 }
 
 // ---------------------------------------------------------------------------
@@ -1743,32 +1771,31 @@ eofa_status eofa_solve_host(eofa_ctx* ctx, const double* rhs, double* sol, const
     eofa_ctx* c = ctx;
     c->err.clear();
     cudaStream_t st = (cudaStream_t)stream;
-    // page-locked host buffers: the import and export kernels read and write
-    // them in place (through NVLink-C2C on a Grace-Blackwell node), with no
-    // staging copies
+    // a page-locked right-hand side (and initial guess) is read in place by
+    // the import kernels (through NVLink-C2C on a Grace-Blackwell node); the
+    // solution is exported to a device field and copied to a page-locked sol
+    // by the copy engine while the true residual is computed
     cudaPointerAttributes ra{}, sa{};
-    const bool direct = cudaPointerGetAttributes(&ra, rhs) == cudaSuccess && ra.type == cudaMemoryTypeHost &&
-                        ra.devicePointer && cudaPointerGetAttributes(&sa, sol) == cudaSuccess &&
-                        sa.type == cudaMemoryTypeHost && sa.devicePointer;
+    const bool rhs_pinned = cudaPointerGetAttributes(&ra, rhs) == cudaSuccess && ra.type == cudaMemoryTypeHost &&
+                            ra.devicePointer;
+    const bool sol_pinned = cudaPointerGetAttributes(&sa, sol) == cudaSuccess && sa.type == cudaMemoryTypeHost &&
+                            sa.devicePointer;
     cudaGetLastError();  // the queries of pageable pointers may leave an error behind
-    if (direct) {
-        eofa_status s = solve_impl(c, (const double*)ra.devicePointer, (double*)sa.devicePointer, *opts, stats, st);
-        if (stats) stats->status = s;
-        CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
-        return s;
-    }
-    double* drhs = act_buf(c, 0);
     double* dsol = act_buf(c, 1);
-    if (!drhs || !dsol) return fail(c, EOFA_ERR_OOM, "work fields of the host solve");
+    double* drhs = rhs_pinned ? (double*)ra.devicePointer : act_buf(c, 0);
+    if (!dsol || !drhs) return fail(c, EOFA_ERR_OOM, "work fields of the host solve");
     const size_t bytes = (size_t)c->n5 * 2 * 24 * sizeof(double);
-    CK(cudaMemcpyAsync(drhs, rhs, bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
-    if (opts->use_guess) CK(cudaMemcpyAsync(dsol, sol, bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
-    eofa_status s = solve_impl(c, drhs, dsol, *opts, stats, st);
-    if (stats) stats->status = s;
-    if (s == EOFA_OK || s == EOFA_ERR_NOT_CONVERGED || s == EOFA_ERR_TIMEOUT || s == EOFA_ERR_NONFINITE) {
-        CK(cudaMemcpyAsync(sol, dsol, bytes, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
-        CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    if (!rhs_pinned) CK(cudaMemcpyAsync(drhs, rhs, bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    const double* guess = nullptr;
+    if (opts->use_guess) {
+        if (sol_pinned) guess = (const double*)sa.devicePointer;
+        else CK(cudaMemcpyAsync(dsol, sol, bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
     }
+    eofa_status s = solve_impl(c, drhs, dsol, *opts, stats, st, sol_pinned ? sol : nullptr, guess);
+    if (stats) stats->status = s;
+    if (!sol_pinned && c->exported)
+        CK(cudaMemcpyAsync(sol, dsol, bytes, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
     return s;
 }
 
@@ -1929,6 +1956,9 @@ void eofa_destroy(eofa_ctx* ctx) {
         }
     }
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    for (cudaEvent_t e : ctx->xev)
+        if (e) cudaEventDestroy(e);
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
     delete ctx;
 }

@@ -1,9 +1,13 @@
 """GPU tests of the host-buffer solve, the device diagnostics and the FMA
 throughput probe.
 
-eofa_solve_host copies a host right-hand side in and the solution out inside
-the call; the answer must be the device solve's (the solver is
-deterministic, so bit for bit) and is judged by the oracle.  eofa_dot must
+eofa_solve_host takes a host right-hand side and writes the solution to host
+memory inside the call (page-locked buffers read in place and filled by the
+copy engine while the true residual is computed, pageable ones staged, in
+every mix); the answer must be the device solve's (the solver is
+deterministic, so bit for bit) and is judged by the oracle.  A zero
+right-hand side gives an exactly zero solution; a non-finite one leaves sol
+untouched.  eofa_dot must
 equal numpy's FP64 inner product (and repeat bit for bit), eofa_force_norms
 the Sec. VI definition evaluated on the host.  The FMA probe must report a
 positive throughput with FP32 above FP64.
@@ -59,6 +63,36 @@ def test_solve_host_matches_device_solve(env, inner):
     # the same restart from page-locked buffers (the guess read in place)
     _, st_gp = s.solve_host(host_rhs, host_sol, tol=1e-10, inner=inner, use_guess=True)
     assert st_gp.status == 0 and st_gp.inner_iters == 0
+    # mixed: page-locked rhs with a pageable sol, and the reverse
+    out_m = np.empty_like(phi)
+    s.solve_host(host_rhs, out_m, tol=1e-10, inner=inner)
+    sol_m = torch.zeros_like(host_rhs).pin_memory()
+    s.solve_host(phi, sol_m, tol=1e-10, inner=inner)
+    assert np.array_equal(out_m, dev.cpu().numpy()) and np.array_equal(sol_m.numpy(), dev.cpu().numpy())
+    s.close()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_solve_host_zero_and_nonfinite_rhs(env, pinned):
+    torch, B, O = env
+    dims, Ls = (4, 4, 4, 4), 8
+    s = B.Solver(I.gauge_field(dims, 0.3, 1), dims, Ls, **ACT)
+
+    def buf(a):
+        t = torch.from_numpy(a)
+        return t.pin_memory() if pinned else t
+
+    zero = buf(np.zeros((4, 4, 4, 4, Ls, 4, 3), dtype=np.complex128))
+    out = buf(np.full((4, 4, 4, 4, Ls, 4, 3), 7.0 + 1j))
+    _, st = s.solve_host(zero, out, tol=1e-10, inner="f32")
+    assert st.status == 0 and st.inner_iters == 0
+    assert torch.count_nonzero(out).item() == 0
+    bad = I.gaussian_fermion(dims, Ls, 5)
+    bad.reshape(-1)[123] = np.nan
+    out = buf(np.full((4, 4, 4, 4, Ls, 4, 3), 7.0 + 1j))
+    _, st = s.solve_host(buf(bad), out, tol=1e-10, inner="f32", check=False)
+    assert st.status == 5  # EOFA_ERR_NONFINITE
+    assert bool((out.numpy() == 7.0 + 1j).all())  # untouched
     s.close()
 
 
