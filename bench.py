@@ -550,6 +550,24 @@ def run_ours(args):
                             "hop_GBps": st.hop_bytes / (st.hop_ms * 1e-3) / 1e9 if st.hop_ms else None,
                             "hop_ms_per_launch": st.hop_ms / st.hop_launches if st.hop_launches else None}
 
+    # the dslash sweep over storage precision x CTA tile shape (cfg 2): the
+    # autotuner's own launch times of every tile variant of the four inner-CG
+    # hop kinds on this lattice, as algorithmic GB/s
+    sweep = {}
+    for name, p in B.PREC.items():
+        row = {}
+        for k in range(4):
+            nbytes = solver.hop_bytes(p, 1 if k in (1, 3) else 0)
+            cells = {}
+            for v in range(4):
+                ms = B.lib().eofa_tile_time(solver.ctx, p, k, v)
+                if ms > 0:
+                    cells[f"v{v}"] = {"us": ms * 1e3, "GBps": nbytes / (ms * 1e-3) / 1e9}
+            if cells:
+                row[f"kind{k}"] = dict(cells, chosen=B.lib().eofa_tile_variant(solver.ctx, p, k))
+        if row:
+            sweep[name] = row
+
     workloads = {}
     if rank == 0 and not args.quick:
         # the paper's comparison (Sec. V.B): even-odd on the unpreconditioned
@@ -632,6 +650,7 @@ def run_ours(args):
         "solve": {"true_res": main["true_res"], "outer_iters": main["outer_iters"],
                   "inner_iters": main["inner_iters"], "kernel_launches_per_solve": launches},
         "other_precisions": extra,
+        "dslash_sweep": sweep,
         "roofline_f64": roofline_f64,
         "speedup_vs_fp64": (f64 / value) if f64 and ws == 1 else None,
         "speedup_vs_fp64_repeats": extra.get("f64", {}).get("repeats"),

@@ -454,6 +454,16 @@ int eofa_tile_sites(const eofa_ctx *ctx, int prec, int kind);
  * first tunes a precision, replaces the timing by that fixed variant. */
 int eofa_tile_variant(const eofa_ctx *ctx, int prec, int kind);
 
+/* The autotuner's measurement behind that choice: milliseconds per launch of
+ * tile variant `variant` (0..3) of hop kernel `kind` in precision prec, the
+ * fastest of three rounds of three launches on the context's own buffers
+ * (the dslash sweep over tile shapes; FP64 has variants 0 and 1 only).  0
+ * when that variant was not timed (not compiled for the precision, the
+ * variant fixed by EOFA_TILE_VARIANT, or no solve in that precision yet);
+ * -1 for invalid arguments.  Contexts of a lattice shape already tuned in the
+ * process report the first context's times. */
+double eofa_tile_time(const eofa_ctx *ctx, int prec, int kind, int variant);
+
 #ifdef __cplusplus
 }
 #endif

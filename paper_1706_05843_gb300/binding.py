@@ -102,6 +102,7 @@ SIGNATURES = {
     "eofa_hop_bytes": ([_vp, C.c_int, C.c_int], C.c_double),
     "eofa_tile_sites": ([_vp, C.c_int, C.c_int], C.c_int),
     "eofa_tile_variant": ([_vp, C.c_int, C.c_int], C.c_int),
+    "eofa_tile_time": ([_vp, C.c_int, C.c_int, C.c_int], C.c_double),
     "eofa_set_system": ([_vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int], C.c_int),
     "eofa_apply_meofa": ([_vp, C.c_double, C.c_double, _vp, _vp, C.POINTER(eofa_solve_opts),
                           C.POINTER(eofa_solve_stats), _vp], C.c_int),

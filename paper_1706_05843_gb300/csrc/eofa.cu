@@ -73,6 +73,7 @@ struct eofa_ctx {
     // autotuned CTA tile variant of the four inner-solver hop kinds, per precision
     bool tuned[4] = {};
     int tile[4][4] = {};
+    float tune_ms[4][4][4] = {};  // [prec][kind][variant] tuner's time per launch (0: not timed)
     // device-driven CG loops, one per inner method and precision
     cudaStream_t cap = nullptr;
     cudaGraphExec_t cg_exec[2][4] = {};
@@ -366,7 +367,11 @@ eofa_status ensure_inner(eofa_ctx* c, int P) {
 // process; tuning happens before any CG graph is captured.
 // ---------------------------------------------------------------------------
 std::mutex g_tune_mu;
-std::map<std::array<long, 5>, int> g_tune_cache;  // (prec, Ls, X*Y, Z*T, kind) -> variant
+struct TuneChoice {
+    int variant = 0;
+    float ms[4] = {0.f, 0.f, 0.f, 0.f};  // per launch of each variant (0: not timed)
+};
+std::map<std::array<long, 5>, TuneChoice> g_tune_cache;  // (prec, Ls, X*Y, Z*T, kind) -> choice
 
 eofa_status autotune(eofa_ctx* c, int P, cudaStream_t st) {
     if (c->tuned[P]) return EOFA_OK;
@@ -385,8 +390,12 @@ eofa_status autotune(eofa_ctx* c, int P, cudaStream_t st) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         for (int k = 0; k < 4; ++k) {
             auto it = g_tune_cache.find({P, g.Ls, (long)g.X * g.Y, (long)g.Z * g.T, k});
-            if (it == g_tune_cache.end()) all = false;
-            else c->tile[P][k] = it->second;
+            if (it == g_tune_cache.end()) {
+                all = false;
+            } else {
+                c->tile[P][k] = it->second.variant;
+                for (int v = 0; v < 4; ++v) c->tune_ms[P][k][v] = it->second.ms[v];
+            }
         }
     }
     if (all) {
@@ -445,6 +454,7 @@ eofa_status autotune(eofa_ctx* c, int P, cudaStream_t st) {
         for (int v = 1; v < nvar; ++v)
             if (best[v] < best[best_v]) best_v = v;
         c->tile[P][k] = forced >= 0 ? forced : best_v;
+        for (int v = 0; v < 4; ++v) c->tune_ms[P][k][v] = (forced < 0 && best[v] < 1e29f) ? best[v] / 3.f : 0.f;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -455,7 +465,11 @@ eofa_status autotune(eofa_ctx* c, int P, cudaStream_t st) {
     }
     c->tuned[P] = true;
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    for (int k = 0; k < 4; ++k) g_tune_cache[{P, g.Ls, (long)g.X * g.Y, (long)g.Z * g.T, k}] = c->tile[P][k];
+    for (int k = 0; k < 4; ++k) {
+        TuneChoice& tc = g_tune_cache[{P, g.Ls, (long)g.X * g.Y, (long)g.Z * g.T, k}];
+        tc.variant = c->tile[P][k];
+        for (int v = 0; v < 4; ++v) tc.ms[v] = c->tune_ms[P][k][v];
+    }
     return EOFA_OK;
 }
 
@@ -1988,6 +2002,11 @@ int eofa_tile_sites(const eofa_ctx* ctx, int prec, int kind) {
 int eofa_tile_variant(const eofa_ctx* ctx, int prec, int kind) {
     if (!ctx || prec < 0 || prec > 3 || kind < 0 || kind > 3) return -1;
     return ctx->tuned[prec] ? ctx->tile[prec][kind] : 0;
+}
+
+double eofa_tile_time(const eofa_ctx* ctx, int prec, int kind, int variant) {
+    if (!ctx || prec < 0 || prec > 3 || kind < 0 || kind > 3 || variant < 0 || variant > 3) return -1.0;
+    return ctx->tuned[prec] ? (double)ctx->tune_ms[prec][kind][variant] : 0.0;
 }
 
 double eofa_hop_bytes(const eofa_ctx* ctx, int prec, int with_local) {

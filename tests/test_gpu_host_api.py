@@ -141,3 +141,23 @@ def test_force_norms_match_definition(env):
     assert rms == pytest.approx(hrms, rel=1e-13)
     assert mx == pytest.approx(hmx, rel=1e-13)
     s.close()
+
+
+def test_tile_sweep_reports_the_tuner(env):
+    """eofa_tile_time gives the autotuner's per-variant launch times (the
+    dslash sweep over tile shapes); the variant it chose is the fastest."""
+    torch, B, O = env
+    dims, Ls = (4, 4, 4, 4), 8
+    s = B.Solver(I.gauge_field(dims, 0.3, 1), dims, Ls, **ACT)
+    lib = B.lib()
+    assert lib.eofa_tile_time(s.ctx, 1, 0, 0) == 0.0          # no FP32 solve yet
+    s.solve(torch.from_numpy(I.gaussian_fermion(dims, Ls, 1001)).cuda(), tol=1e-10, inner="f32")
+    for prec, nvar in [(1, 4), (0, 2)]:                         # FP32 inner, FP64 outer kinds
+        for k in range(4):
+            t = [lib.eofa_tile_time(s.ctx, prec, k, v) for v in range(4)]
+            timed = [x for x in t if x > 0]
+            assert 2 <= len(timed) <= nvar, (prec, k, t)
+            assert t[lib.eofa_tile_variant(s.ctx, prec, k)] == min(timed)
+    assert lib.eofa_tile_time(s.ctx, 1, 0, 4) == -1.0
+    assert lib.eofa_tile_time(s.ctx, 0, 0, 2) == 0.0             # FP64 has two variants
+    s.close()
