@@ -15,7 +15,8 @@ inner restarts.
   beside systems that start from an initial guess, the iteration cap
   (EOFA_ERR_NOT_CONVERGED with the best solution written), and a deadline
   (EOFA_ERR_TIMEOUT from the device decision), after which the same
-  contexts solve to 1e-10.
+  contexts solve to 1e-10; a G-parity context (twice the 5D volume, two
+  flavours) in one batch with ordinary ones.
 """
 import numpy as np
 import pytest
@@ -171,4 +172,31 @@ def test_batched_deadline(env):
     for i in range(len(rhs)):
         assert st[i].status == 0
         assert rel(oracles[i].hsys(sols[i].cpu().numpy()), rhs[i].cpu().numpy()) <= 1e-10
+    close(solvers)
+
+
+def test_batched_with_gparity_context(env):
+    """A G-parity context (two flavours stacked along t, flavour-changing
+    boundary hops) in one batch with an ordinary one; each judged by its own
+    oracle and equal to its one-by-one solve."""
+    torch, B, O = env
+    from oracle.gparity import GOracle
+    dims, Ls, gm = (4, 4, 2, 4), 8, 3
+    act = dict(MOB, beta=-1.0, pm=1)
+    U = I.gauge_field(dims, 0.5, 21)
+    sg = B.Solver(U, dims, Ls, gparity=gm, **act)
+    og = GOracle(O.Action(dims=dims, Ls=Ls, **act), U, gm)
+    phig = np.stack([I.gaussian_fermion(dims, Ls, 3000), I.gaussian_fermion(dims, Ls, 3001)])
+    solvers, oracles, rhs = make_batch(env, BATCH[:2])
+    solvers.insert(0, sg)
+    rhs.insert(0, torch.from_numpy(phig).cuda())
+    sols = [torch.empty_like(r) for r in rhs]
+    st = B.eofa_solve_batched([s.ctx for s in solvers], rhs, sols, B.make_opts(tol=1e-10, inner="f32"))
+    assert all(x.status == 0 for x in st)
+    assert rel(og.hsys(sols[0].cpu().numpy()), phig) <= 1e-10
+    for i in (1, 2):
+        assert rel(oracles[i - 1].hsys(sols[i].cpu().numpy()), rhs[i].cpu().numpy()) <= 1e-10
+    one, st1 = sg.solve(rhs[0], tol=1e-10, inner="f32")
+    assert (st[0].outer_iters, st[0].inner_iters) == (st1.outer_iters, st1.inner_iters)
+    assert rel(sols[0].cpu().numpy(), one.cpu().numpy()) < 1e-12
     close(solvers)
