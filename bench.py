@@ -613,7 +613,11 @@ def run_ours(args):
                 "timing": "CUDA events recorded inside the solver's CUDA graph on the solve stream around the "
                           "four hop launches of one CG iteration per inner solve, over the timed steps",
                 "tile_variants": tiles,
-                "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+                "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                # the same launches by their measured DRAM traffic (ncu bytes per
+                # launch / CUDA-event time) and against the nominal HBM3e rate
+                "dram_achieved": traffic / (hop_ms / hop_n * 1e-3) / 1e9 if traffic and hop_n and hop_ms else None,
+                "frac_of_nominal_7900": achieved / 7900.0 if achieved else None}
     cpu = None
     if ws == 1 and not args.no_cpu:
         pi, n_iter, cores = oracle_sample(args.ref_iters)
