@@ -1925,6 +1925,7 @@ eofa_status eofa_apply_batched(eofa_ctx* const* ctx, int n, const void* const* i
 eofa_status eofa_solve_batched(eofa_ctx* const* ctx, int n, const void* const* rhs, void* const* sol,
                                const eofa_solve_opts* opts, eofa_solve_stats* stats, void* stream) {
     if (n < 0 || (n > 0 && (!ctx || !rhs || !sol || !opts))) return EOFA_ERR_ARG;
+    if (n == 0) return EOFA_OK;  // nothing to solve (opts may be NULL)
     for (int i = 0; i < n; ++i) {
         if (!ctx[i] || !rhs[i] || !sol[i] || rhs[i] == sol[i]) return EOFA_ERR_ARG;
         for (int j = 0; j < i; ++j)

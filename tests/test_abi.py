@@ -109,3 +109,13 @@ def test_argument_errors_without_gpu(libeofa):
     assert libeofa.eofa_force(None, 0.04, 1.0, None, None, C.byref(opts), None, None) == 1
     assert libeofa.eofa_heatbath(None, 0.04, 1.0, 0, None, None, None, 0, None, None, C.byref(opts), None,
                                  None) == 1
+
+
+def test_empty_batches_are_no_ops(libeofa):
+    """n = 0 returns EOFA_OK before touching any pointer or the device."""
+    from paper_1706_05843_gb300 import binding as B
+    opts = B.make_opts(tol=1e-10)
+    assert libeofa.eofa_solve_batched(None, 0, None, None, C.byref(opts), None, None) == 0
+    assert libeofa.eofa_solve_batched(None, 0, None, None, None, None, None) == 0
+    assert libeofa.eofa_apply_batched(None, 0, None, None, 0, None) == 0
+    assert libeofa.eofa_solve_batched(None, -1, None, None, None, None, None) == 1

@@ -214,6 +214,30 @@ def test_solve_batched_uneven_lattices(env, inner):
         s.close()
 
 
+def test_equal_shift_masses_collapse_to_the_plain_system(env):
+    """m3 = m2 zeroes k(m2, m3): the library's H + beta Delta P with beta = -1
+    equals its beta = 0 operator, the oracle's H(m1), and its solve is judged
+    by the plain system (the Sherman-Morrison factors degenerate to 1)."""
+    torch, B, O = env
+    dims, Ls = (4, 4, 4, 4), 8
+    U = I.gauge_field(dims, 0.3, 1)
+    act = dict(MOB, beta=-1.0, pm=1, m2=0.5, m3=0.5)
+    s1 = B.Solver(U, dims, Ls, **act)
+    s0 = B.Solver(U, dims, Ls, **dict(act, beta=0.0))
+    o0 = O.Oracle(O.Action(dims=dims, Ls=Ls, **dict(act, beta=0.0)), U)
+    psi = I.gaussian_fermion(dims, Ls, 7)
+    x = torch.from_numpy(psi).cuda()
+    h1 = s1.apply_h(x).cpu().numpy()
+    assert rel(h1, s0.apply_h(x).cpu().numpy()) < 1e-14
+    assert rel(h1, o0.hsys(psi)) < 1e-12
+    phi = I.gaussian_fermion(dims, Ls, 1001)
+    for s in (s1, s0):
+        out, st = s.solve(torch.from_numpy(phi).cuda(), tol=1e-10, inner="f32")
+        assert rel(o0.hsys(out.cpu().numpy()), phi) <= 1e-10
+    s1.close()
+    s0.close()
+
+
 def test_solve_batched_rejects_duplicate_context(env):
     torch, B, O = env
     torch_, s, o = setup(env, CASES[0])

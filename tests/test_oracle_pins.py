@@ -454,6 +454,20 @@ def test_beta_zero_reduces_to_dwf(oracle_mod):
     assert rel(o.asys(psi), o.deofa(psi, o.a.m1)) < 1e-15
 
 
+def test_equal_shift_masses_remove_the_shift(oracle_mod):
+    """k(m2, m3) of App. A carries the factor (m3 - m2): with m3 = m2 the
+    shift vanishes for any beta and the system is H(m1) alone; with m3 != m2
+    it does not (the check is not vacuous)."""
+    psi = I.gaussian_fermion((4, 4, 4, 4), 8, 3)
+    for pm in (1, -1):
+        o1 = make(oracle_mod, beta=-1.0, pm=pm, m1=0.04, m2=0.5, m3=0.5, **MOBIUS)
+        o0 = make(oracle_mod, beta=0.0, pm=pm, m1=0.04, m2=0.5, m3=0.5, **MOBIUS)
+        assert rel(o1.hsys(psi), o0.hsys(psi)) < 1e-15
+        assert rel(o1.k(psi), o0.k(psi)) < 1e-15
+        o2 = make(oracle_mod, beta=-1.0, pm=pm, m1=0.04, m2=0.5, m3=0.6, **MOBIUS)
+        assert rel(o2.hsys(psi), o0.hsys(psi)) > 1e-6
+
+
 @pytest.mark.parametrize("name", ["k", "asys", "ddwf", "deofa", "dw5", "dtilde", "L"])
 def test_adjoints(oracle_mod, name):
     o = make(oracle_mod, dims=(4, 2, 2, 4), Ls=6, beta=0.7, m3=0.3, **MOBIUS2)
