@@ -119,3 +119,24 @@ def test_empty_batches_are_no_ops(libeofa):
     assert libeofa.eofa_solve_batched(None, 0, None, None, None, None, None) == 0
     assert libeofa.eofa_apply_batched(None, 0, None, None, 0, None) == 0
     assert libeofa.eofa_solve_batched(None, -1, None, None, None, None, None) == 1
+
+
+def test_more_argument_errors_without_gpu(libeofa):
+    """The remaining entry points reject missing arguments before any device
+    work; the queries answer for a missing context without touching it."""
+    from paper_1706_05843_gb300 import binding as B
+    assert libeofa.eofa_apply_dag(None, None, None, None) == 1
+    assert libeofa.eofa_apply_h(None, None, None, None) == 1
+    p = B.make_params((4, 4, 4, 4), 8)
+    assert libeofa.eofa_apply_noalloc(C.byref(p), None, None, None, None) == 1
+    dims = (C.c_int * 4)(4, 4, 4, 4)
+    assert libeofa.eofa_net_forward(None, dims, 1, None, None, None) == 1
+    assert libeofa.eofa_net_forward(None, None, 1, None, None, None) == 1
+    assert libeofa.eofa_net_backward(None, dims, 1, None, None, None, None, None) == 1
+    assert libeofa.eofa_set_preconditioner(None, None) == 1
+    assert libeofa.eofa_train_preconditioner(None, None, 0, None, None, None, None, None) == 1
+    assert libeofa.eofa_last_error(None) == b""
+    assert libeofa.eofa_tile_variant(None, 1, 0) == -1
+    assert libeofa.eofa_tile_time(None, 1, 0, 0) == -1.0
+    assert libeofa.eofa_hop_bytes(None, 1, 0) == 0.0
+    libeofa.eofa_destroy(None)  # a no-op
