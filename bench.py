@@ -389,6 +389,40 @@ def run_learned(B, I, torch, dev):
     return res
 
 
+def run_profile_net(args):
+    """One forward pass of the learned preconditioner's network at 16^3x32
+    with 16 slices (2,097,152 rows; three tcgen05 convolutions), after a
+    warm-up pass, timed with CUDA events; prints one JSON line (the command
+    the ncu captures of k_conv_tc run)."""
+    import torch
+    from paper_1706_05843_gb300 import binding as B
+    from paper_1706_05843_gb300 import build as BLD
+    torch.cuda.set_device(0)
+    if not os.path.exists(B.LIB_PATH):
+        BLD.build()
+    B.lib()
+    dims, S = (16, 16, 16, 32), 16
+    rng = np.random.default_rng(17)
+    w = np.concatenate([rng.standard_normal(81 * co * ci) * np.sqrt(2.0 / (81 * ci))
+                        for ci, co in [(24, 32), (32, 32), (32, 24)]]).astype(np.float32)
+    X, Y, Z, T = dims
+    x = torch.from_numpy(rng.standard_normal((S, T, Z, Y, X, 24)).astype(np.float32)).cuda()
+    out = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    B.eofa_net_forward(w, dims, x, out, stream=stream)  # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    B.eofa_net_forward(w, dims, x, out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rows = X * Y * Z * T * S
+    flops = 2.0 * rows * 3 * 81 * 32 * 32  # executed: 3 layers, 81 taps, 32 x 32 padded channels
+    print(json.dumps({"profile_net": True, "rows": rows, "ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+                      "frac_of_bf16_burst": flops / (ms * 1e-3) / 1e12 / bf16_peaks()[0]}))
+
+
 def run_fma_peaks(args):
     """FP64 and FP32 FMA throughput of GPU 0 (eofa_measure_fma, best of 5
     launches each, repeated for about 4 s) with nvidia-smi clock samples
@@ -684,11 +718,17 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="timed solves with the host-driven CG loop and every hop timed (ncu launch lists: "
                          "ncu does not profile the kernels inside the solver's conditional graph nodes)")
+    ap.add_argument("--profile-net", action="store_true",
+                    help="only one forward pass of the learned preconditioner's network at 16^3x32, 16 slices "
+                         "(for ncu captures of the tcgen05 convolution)")
     ap.add_argument("--fma-peaks", action="store_true",
                     help="only measure the FP64/FP32 FMA throughput with clock samples and print it")
     args = ap.parse_args()
     if args.fma_peaks:
         run_fma_peaks(args)
+        return
+    if args.profile_net:
+        run_profile_net(args)
         return
     if args.profile:
         args.quick, args.no_cpu, args.steps, args.warmup, args.no_learned = True, True, 1, 0, True
