@@ -662,7 +662,7 @@ def run_ours(args):
                              f"iterations to r=1e-10"}
     f64 = extra.get("f64", {}).get("s_per_solve")
     # the FP64 hop (the plain FP64 CG comparator) against the measured FP64
-    # FMA throughput: SURVEY-style count of 1520 flops per 5D output site per
+    # FMA throughput: an algorithmic count of 1520 flops per 5D output site per
     # launch (1320 Wilson hop, 50 for b5 + c5 L, 150 for the s-space inverse)
     roofline_f64 = None
     if rank == 0 and not args.quick and extra.get("f64", {}).get("hop_ms_per_launch"):
