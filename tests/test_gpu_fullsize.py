@@ -8,7 +8,7 @@ times, judged by the FP64 oracle on the whole lattice.
   ||phi - (H + beta Delta P) psi|| / ||phi|| <= 1e-10 for the H form (the
   stopping tolerance of the defect-correction scheme, Sec. V.A) and
   ||b - K psi'|| / ||b|| <= 1e-10 for the K form (App. B), at 16^3x32 Ls=16
-  with FP64, FP32, FP16 and BF16 inner storage and at 24^3x64 Ls=12 with FP16
+  with FP64, FP32, FP16 and BF16 inner storage and at 24^3x64 Ls=12 with FP32, FP16
   and BF16 inner storage for each of its four right-hand sides; the GPU's own
   true residual agrees with the oracle's.
 * The batched workload (16 right-hand sides, 8 on 16^4 Ls=16 and 8 on
@@ -128,7 +128,7 @@ def test_fullsize_apply_whole_lattice_24c64(env):
     check_apply(env, CFG3)
 
 
-@pytest.mark.parametrize("inner", ["f16", "bf16"])
+@pytest.mark.parametrize("inner", ["f16", "bf16", "f32"])
 def test_fullsize_24c64_solves_judged_by_oracle(env, inner):
     """24^3x64 Ls=12, m = 0.0362, the four right-hand sides of the workload."""
     torch = env[0]
