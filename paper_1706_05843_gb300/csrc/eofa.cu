@@ -175,7 +175,7 @@ void host_inv(int Ls, double a, double g, double m, const double* v, double* t) 
 }
 // solve (a + g L-) t = v
 void host_invT(int Ls, double a, double g, double m, const double* v, double* t) {
-    double vr[LSMAX], tr[LSMAX];
+    double vr[LSMAX] = {}, tr[LSMAX] = {};
     for (int s = 0; s < Ls; ++s) vr[s] = v[Ls - 1 - s];
     host_inv(Ls, a, g, m, vr, tr);
     for (int s = 0; s < Ls; ++s) t[s] = tr[Ls - 1 - s];
