@@ -1256,7 +1256,10 @@ eofa_status solve_batched_impl(eofa_ctx* const* cs, int n, const void* const* rh
         if (e != cudaSuccess) return cuda_fail(cs[0], e, "batched solve start");
     }
     for (int i = 0; i < n; ++i)
-        if ((s = solve_check_rhs(cs[i], (double*)sol[i], ss[i], st))) return s;
+        if ((s = solve_check_rhs(cs[i], (double*)sol[i], ss[i], st))) {
+            if (i > 0) cs[0]->err = "system " + std::to_string(i) + ": " + cs[i]->err;
+            return s;
+        }
     const int P = ss[0].P;
     std::vector<long> launches0(n);
     for (int i = 0; i < n; ++i) launches0[i] = cs[i]->launches;

@@ -200,3 +200,24 @@ def test_batched_with_gparity_context(env):
     assert (st[0].outer_iters, st[0].inner_iters) == (st1.outer_iters, st1.inner_iters)
     assert rel(sols[0].cpu().numpy(), one.cpu().numpy()) < 1e-12
     close(solvers)
+
+
+def test_batched_non_finite_rhs(env):
+    """A NaN in one system's right-hand side stops the call with
+    EOFA_ERR_NONFINITE at the source-norm check, before the device loop; the
+    same contexts then solve a clean batch to 1e-10."""
+    torch, B, O = env
+    solvers, oracles, rhs = make_batch(env)
+    ctxs = [s.ctx for s in solvers]
+    bad = [r.clone() for r in rhs]
+    bad[2].view(-1)[17] = float("nan")
+    sols = [torch.empty_like(r) for r in rhs]
+    with pytest.raises(B.EofaError) as e:
+        B.eofa_solve_batched(ctxs, bad, sols, B.make_opts(tol=1e-10, inner="f32"))
+    assert e.value.status == 5
+    assert "system 2" in str(e.value)
+    st = B.eofa_solve_batched(ctxs, rhs, sols, B.make_opts(tol=1e-10, inner="f32"))
+    for i in range(len(rhs)):
+        assert st[i].status == 0
+        assert rel(oracles[i].hsys(sols[i].cpu().numpy()), rhs[i].cpu().numpy()) <= 1e-10
+    close(solvers)
