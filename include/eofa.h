@@ -303,7 +303,10 @@ eofa_status eofa_apply_batched(eofa_ctx *const *ctx, int n, const void *const *i
  * eofa_set_system or eofa_destroy of any of them).  Each system's outer
  * steps and inner iterations equal those of its eofa_solve.  With
  * opts->kernel_timing, opts->precond or opts->method set the systems are
- * solved one by one.  Contexts must be distinct. */
+ * solved one by one.  Contexts must be distinct.  More than 32 systems run
+ * as several graphs of at most 32.  The message of a failing status is
+ * reported on ctx[0] (eofa_last_error), prefixed "system i: " when it
+ * belongs to another system. */
 eofa_status eofa_solve_batched(eofa_ctx *const *ctx, int n, const void *const *rhs,
                                void *const *sol, const eofa_solve_opts *opts,
                                eofa_solve_stats *stats, void *stream);

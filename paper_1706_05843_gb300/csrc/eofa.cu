@@ -1240,14 +1240,18 @@ eofa_status batch_graph(eofa_ctx* const* cs, int n, int P, cudaGraphExec_t* exec
     return EOFA_OK;
 }
 
+// *failed: the system whose context holds the message of a failing status
+// (0 for failures of the batch as a whole, reported on cs[0]).
 eofa_status solve_batched_impl(eofa_ctx* const* cs, int n, const void* const* rhs, void* const* sol,
-                               const eofa_solve_opts& o, eofa_solve_stats* stats, cudaStream_t st) {
+                               const eofa_solve_opts& o, eofa_solve_stats* stats, cudaStream_t st,
+                               int* failed) {
     std::vector<SolveState> ss(n);
     eofa_status s;
+    *failed = 0;
     for (int i = 0; i < n; ++i) {
         cs[i]->err.clear();
         if ((s = solve_begin(cs[i], (const double*)rhs[i], (const double*)sol[i], o, ss[i], st))) {
-            if (i > 0) cs[0]->err = "system " + std::to_string(i) + ": " + cs[i]->err;
+            *failed = i;
             return s;
         }
     }
@@ -1257,7 +1261,7 @@ eofa_status solve_batched_impl(eofa_ctx* const* cs, int n, const void* const* rh
     }
     for (int i = 0; i < n; ++i)
         if ((s = solve_check_rhs(cs[i], (double*)sol[i], ss[i], st))) {
-            if (i > 0) cs[0]->err = "system " + std::to_string(i) + ": " + cs[i]->err;
+            *failed = i;
             return s;
         }
     const int P = ss[0].P;
@@ -1308,7 +1312,10 @@ eofa_status solve_batched_impl(eofa_ctx* const* cs, int n, const void* const* rh
     eofa_status first = EOFA_OK;
     for (int i = 0; i < n; ++i) {
         s = solve_end(cs[i], (double*)sol[i], o, ss[i], stats ? stats + i : nullptr, st);
-        if (s != EOFA_OK && first == EOFA_OK) first = s;
+        if (s != EOFA_OK && first == EOFA_OK) {
+            first = s;
+            *failed = i;
+        }
     }
     return first;
 }
@@ -1937,22 +1944,31 @@ eofa_status eofa_solve_batched(eofa_ctx* const* ctx, int n, const void* const* r
     // kernel timing instruments the host-driven loop, the learned
     // preconditioner runs flexible GCR, and the dense comparison scheme has
     // no batched loop: these solve one by one
+    // errors are reported on the first context, prefixed with the system
+    auto report = [&](int k) {
+        if (k > 0) ctx[0]->err = "system " + std::to_string(k) + ": " + ctx[k]->err;
+    };
     if (opts->kernel_timing || opts->precond || opts->method || opts->inner < 0 || opts->inner > 3) {
         eofa_status first = EOFA_OK;
         for (int i = 0; i < n; ++i) {
             eofa_status s = eofa_solve(ctx[i], rhs[i], sol[i], opts, stats ? stats + i : nullptr, stream);
-            if (s != EOFA_OK && first == EOFA_OK) first = s;
+            if (s != EOFA_OK && first == EOFA_OK) {
+                first = s;
+                report(i);
+            }
         }
         return first;
     }
     eofa_status first = EOFA_OK;
     for (int lo = 0; lo < n; lo += kBatchMax) {
         const int m = std::min(kBatchMax, n - lo);
+        int failed = 0;
         eofa_status s = solve_batched_impl(ctx + lo, m, rhs + lo, sol + lo, *opts, stats ? stats + lo : nullptr,
-                                           (cudaStream_t)stream);
-        if (stats)
-            for (int i = 0; i < m; ++i) stats[lo + i].status = stats[lo + i].status ? stats[lo + i].status : 0;
-        if (s != EOFA_OK && first == EOFA_OK) first = s;
+                                           (cudaStream_t)stream, &failed);
+        if (s != EOFA_OK && first == EOFA_OK) {
+            first = s;
+            report(lo + failed);
+        }
     }
     return first;
 }

@@ -145,6 +145,7 @@ def test_batched_iteration_cap(env):
     sols = [torch.empty_like(r) for r in rhs]
     st = B.eofa_solve_batched([s.ctx for s in solvers], rhs, sols,
                               B.make_opts(tol=1e-10, inner="f32", max_iter=20), check=False)
+    assert B.lib().eofa_last_error(solvers[0].ctx).decode() == "iteration cap"
     for i in range(len(rhs)):
         assert st[i].status == NOT_CONVERGED
         assert 20 <= st[i].inner_iters < 20 + CHUNK
@@ -220,4 +221,29 @@ def test_batched_non_finite_rhs(env):
     for i in range(len(rhs)):
         assert st[i].status == 0
         assert rel(oracles[i].hsys(sols[i].cpu().numpy()), rhs[i].cpu().numpy()) <= 1e-10
+    close(solvers)
+
+
+def test_batched_more_systems_than_one_graph(env):
+    """34 systems: the call runs them as graphs of at most 32; all are judged
+    by the oracle, and a failure in the second graph is reported on the
+    first context with its system index."""
+    torch, B, O = env
+    dims, Ls = (2, 2, 2, 6), 4
+    act = dict(MOB, beta=-1.0, pm=1)
+    U = I.gauge_field(dims, 0.5, 5)
+    o = O.Oracle(O.Action(dims=dims, Ls=Ls, **act), U)
+    solvers = [B.Solver(U, dims, Ls, **act) for _ in range(34)]
+    ctxs = [s.ctx for s in solvers]
+    rhs = [torch.from_numpy(I.gaussian_fermion(dims, Ls, 4000 + i)).cuda() for i in range(34)]
+    sols = [torch.empty_like(r) for r in rhs]
+    st = B.eofa_solve_batched(ctxs, rhs, sols, B.make_opts(tol=1e-10, inner="f32"))
+    for i in range(34):
+        assert st[i].status == 0
+        assert rel(o.hsys(sols[i].cpu().numpy()), rhs[i].cpu().numpy()) <= 1e-10
+    bad = [r.clone() for r in rhs]
+    bad[33].view(-1)[3] = float("inf")
+    with pytest.raises(B.EofaError) as e:
+        B.eofa_solve_batched(ctxs, bad, sols, B.make_opts(tol=1e-10, inner="f32"))
+    assert e.value.status == 5 and "system 33" in str(e.value)
     close(solvers)
