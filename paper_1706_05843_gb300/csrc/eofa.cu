@@ -2453,7 +2453,10 @@ extern "C" eofa_status eofa_train_preconditioner(eofa_ctx* ctx, const void* cons
     if (opts->pairs <= 0 || opts->snapshot_every <= 0 || opts->epochs <= 0 || opts->batch <= 0 || !(opts->lr > 0.0) ||
         !(opts->solve_tol > 0.0) || opts->holdout < 0)
         return EOFA_ERR_ARG;
+    for (int i = 0; i < n_sources; ++i)
+        if (!sources[i]) return EOFA_ERR_ARG;
     eofa_ctx* c = ctx;
+    c->err.clear();
     cudaStream_t st = (cudaStream_t)stream;
     const auto t0 = Clock::now();
     eofa_status s;

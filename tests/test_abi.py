@@ -135,6 +135,11 @@ def test_more_argument_errors_without_gpu(libeofa):
     assert libeofa.eofa_net_backward(None, dims, 1, None, None, None, None, None) == 1
     assert libeofa.eofa_set_preconditioner(None, None) == 1
     assert libeofa.eofa_train_preconditioner(None, None, 0, None, None, None, None, None) == 1
+    # a missing source among the sources (no context needed to reject it)
+    w = (C.c_float * B.NET_WEIGHTS)()
+    topts = B.make_train_opts()
+    srcs = (C.c_void_p * 2)(1, None)
+    assert libeofa.eofa_train_preconditioner(C.c_void_p(1), srcs, 2, w, C.byref(topts), w, None, None) == 1
     assert libeofa.eofa_last_error(None) == b""
     assert libeofa.eofa_tile_variant(None, 1, 0) == -1
     assert libeofa.eofa_tile_time(None, 1, 0, 0) == -1.0
