@@ -146,6 +146,14 @@ def _dptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _need(a, n, what):
+    """The library takes plain pointers: a field of another size would be
+    read or written past its end, so the Solver checks sizes first."""
+    size = a.size if isinstance(a, np.ndarray) else a.numel()
+    if size != n:
+        raise ValueError(f"{what}: {size} complex elements, the context needs {n}")
+
+
 def _check(ctx, status):
     if status != 0:
         msg = lib().eofa_last_error(ctx).decode() if ctx else ""
@@ -401,6 +409,9 @@ class Solver:
             gauge = torch.from_numpy(np.ascontiguousarray(gauge)).cuda()
         self.params = make_params(dims, Ls, **action)
         self.dims, self.Ls, self.gparity = tuple(dims), int(Ls), int(gparity)
+        self.ctx = None
+        X, Y, Z, T = self.dims
+        _need(gauge, X * Y * Z * T * 4 * 9, "gauge field")
         if self.gparity:
             self.ctx = eofa_create_gparity(self.params, gauge, self.gparity, stream)
         else:
@@ -419,23 +430,37 @@ class Solver:
         import torch
         return torch.empty(self.shape5, dtype=torch.complex128, device="cuda")
 
+    @property
+    def _n5(self):
+        return int(np.prod(self.shape5))
+
+    @property
+    def _n4(self):
+        return int(np.prod(self.shape4))
+
     def apply(self, x, dag=False, stream=None):
+        _need(x, self._n5, "input field")
         out = self._new()
         (eofa_apply_dag if dag else eofa_apply)(self.ctx, x, out, stream)
         return out
 
     def apply_h(self, x, stream=None):
+        _need(x, self._n5, "input field")
         out = self._new()
         eofa_apply_h(self.ctx, x, out, stream)
         return out
 
     def solve(self, rhs, stream=None, out=None, check=True, **opts):
+        _need(rhs, self._n5, "right-hand side")
         sol = self._new() if out is None else out
+        _need(sol, self._n5, "solution")
         st = eofa_solve(self.ctx, rhs, sol, make_opts(**opts), stream, check=check)
         return sol, st
 
     def solve_host(self, rhs, out, stream=None, check=True, **opts):
         """Solve with host rhs and host out (numpy complex128 or CPU tensors)."""
+        _need(rhs, self._n5, "right-hand side")
+        _need(out, self._n5, "solution")
         st = eofa_solve_host(self.ctx, rhs, out, make_opts(**opts), stream, check=check)
         return out, st
 
@@ -453,6 +478,7 @@ class Solver:
     def apply_meofa(self, phi, m1, m2, stream=None, check=True, **opts):
         """M_EOFA(m1, m2) phi for a 4D field; returns (out, [minus, plus] stats)."""
         import torch
+        _need(phi, self._n4, "4D field")
         out = torch.empty(self.shape4, dtype=torch.complex128, device="cuda")
         st = eofa_apply_meofa(self.ctx, m1, m2, phi, out, make_opts(**opts), stream, check)
         return out, st
@@ -461,6 +487,7 @@ class Solver:
         """EOFA pseudofermion force sum_a T^a d^a S per link, shape
         (T, Z, Y, X, 4, 3, 3); returns (force, [chi_1, chi_2] stats)."""
         import torch
+        _need(phi, self._n4, "4D field")
         X, Y, Z, T = self.dims
         f = torch.empty((T, Z, Y, X, 4, 3, 3), dtype=torch.complex128, device="cuda")
         st = eofa_force(self.ctx, m1, m2, phi, f, make_opts(**opts), stream, check)
@@ -472,6 +499,8 @@ class Solver:
 
     def force_norms(self, force, stream=None):
         """(F_RMS, F_max) of a force from Solver.force (Sec. VI)."""
+        X, Y, Z, T = self.dims
+        _need(force, X * Y * Z * T * 4 * 9, "force")
         return eofa_force_norms(self.ctx, force, stream)
 
     def heatbath(self, eta, m1, m2, approx, pole_tol=None, forecast=0, stream=None, check=True, **opts):
@@ -479,13 +508,15 @@ class Solver:
         (alpha0, alpha, beta attributes, e.g. rational.InvSqrt); returns
         (phi, stats of the 2 N_p solves)."""
         import torch
+        _need(eta, self._n4, "4D field")
         phi = torch.empty(self.shape4, dtype=torch.complex128, device="cuda")
         st = eofa_heatbath(self.ctx, m1, m2, approx.alpha0, approx.alpha, approx.beta, eta, phi,
                            make_opts(**opts), pole_tol, forecast, stream, check)
         return phi, st
 
     def close(self):
-        eofa_destroy(self.ctx)
+        if self.ctx is not None:
+            eofa_destroy(self.ctx)
         self.ctx = None
 
     def __del__(self):

@@ -161,3 +161,26 @@ def test_tile_sweep_reports_the_tuner(env):
     assert lib.eofa_tile_time(s.ctx, 1, 0, 4) == -1.0
     assert lib.eofa_tile_time(s.ctx, 0, 0, 2) == 0.0             # FP64 has two variants
     s.close()
+
+
+def test_solver_rejects_fields_of_another_size(env):
+    """The C ABI takes plain pointers; the Solver checks every field's size
+    before a call, so a field of another lattice never reaches a kernel."""
+    torch, B, O = env
+    dims, Ls = (4, 4, 4, 4), 8
+    U = I.gauge_field(dims, 0.3, 1)
+    with pytest.raises(ValueError):
+        B.Solver(U[:2], dims, Ls, **ACT)
+    s = B.Solver(U, dims, Ls, **ACT)
+    small = torch.zeros((2, 2, 2, 2, Ls, 4, 3), dtype=torch.complex128, device="cuda")
+    for call in (lambda: s.apply(small), lambda: s.apply_h(small), lambda: s.solve(small),
+                 lambda: s.solve_host(small.cpu().numpy(), small.cpu().numpy()),
+                 lambda: s.force_norms(small), lambda: s.heatbath(small, 0.04, 1.0, None)):
+        with pytest.raises(ValueError):
+            call()
+    phi = torch.from_numpy(I.gaussian_fermion(dims, Ls, 1001)).cuda()
+    with pytest.raises(ValueError):
+        s.solve(phi, out=small)
+    _, st = s.solve(phi, tol=1e-10, inner="f32")      # the context is unharmed
+    assert st.status == 0
+    s.close()
