@@ -398,6 +398,20 @@ def eofa_hop_bytes(ctx, prec, with_local):
     return float(lib().eofa_hop_bytes(ctx, int(prec), int(with_local)))
 
 
+def solve_batched(solvers, rhs, out=None, stream=None, check=True, **opts):
+    """eofa_solve_batched over Solver objects (one right-hand side each),
+    with every field's size checked against its solver; returns (solutions,
+    per-system stats)."""
+    if len(rhs) != len(solvers) or (out is not None and len(out) != len(solvers)):
+        raise ValueError("one right-hand side (and solution) per solver")
+    sols = [s._new() for s in solvers] if out is None else list(out)
+    for s, r, x in zip(solvers, rhs, sols):
+        _need(r, s._n5, "right-hand side")
+        _need(x, s._n5, "solution")
+    st = eofa_solve_batched([s.ctx for s in solvers], rhs, sols, make_opts(**opts), stream, check=check)
+    return sols, st
+
+
 class Solver:
     """Context owner: Solver(gauge, dims, Ls, **action) then apply / solve.
     gparity: 0, or the bit mask of G-parity directions (bit 0 = x .. bit 3 =

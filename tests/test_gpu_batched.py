@@ -89,6 +89,21 @@ def test_batched_equals_one_by_one(env, inner):
     close(solvers)
 
 
+def test_solve_batched_helper_checks_sizes(env):
+    """binding.solve_batched: the same solutions as the C-named call, and a
+    right-hand side of another lattice is refused before the library."""
+    torch, B, O = env
+    solvers, oracles, rhs = make_batch(env)
+    sols, st = B.solve_batched(solvers, rhs, tol=1e-10, inner="f32")
+    ref = [torch.empty_like(r) for r in rhs]
+    B.eofa_solve_batched([s.ctx for s in solvers], rhs, ref, B.make_opts(tol=1e-10, inner="f32"))
+    for i in range(len(rhs)):
+        assert st[i].status == 0 and torch.equal(sols[i], ref[i])
+    with pytest.raises(ValueError):
+        B.solve_batched(solvers, [rhs[1], rhs[0]] + rhs[2:], tol=1e-10, inner="f32")
+    close(solvers)
+
+
 def test_batched_kept_graph_repeat_and_set_system(env):
     torch, B, O = env
     solvers, oracles, rhs = make_batch(env)
