@@ -336,6 +336,23 @@ def _f32ptr(a):
     return a, a.ctypes.data_as(_fp)
 
 
+def _weights(w):
+    """The network's weights as host float32: the library copies exactly
+    NET_WEIGHTS of them."""
+    a, p = _f32ptr(w)
+    if a.size != NET_WEIGHTS:
+        raise ValueError(f"weights: {a.size} values, the network has {NET_WEIGHTS}")
+    return a, p
+
+
+def _net_rows(dims, *fields):
+    """Every network field holds (slices, T, Z, Y, X, 24) float32 values."""
+    n = int(fields[0].shape[0]) * int(np.prod([int(x) for x in dims])) * 24
+    for f in fields:
+        if f is not None and f.numel() != n:
+            raise ValueError(f"network field: {f.numel()} values, the lattice and slice count need {n}")
+
+
 def _f32dev(t):
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
@@ -345,14 +362,16 @@ def _f32dev(t):
 
 def eofa_net_forward(weights, dims, inp, out, stream=None):
     """out = net(inp); inp, out: float32 CUDA tensors (S, T, Z, Y, X, 24)."""
-    w, wp = _f32ptr(weights)
+    w, wp = _weights(weights)
+    _net_rows(dims, inp, out)
     d = (C.c_int * 4)(*[int(x) for x in dims])
     _check(None, lib().eofa_net_forward(wp, d, int(inp.shape[0]), _f32dev(inp), _f32dev(out), _stream(stream)))
 
 
 def eofa_net_backward(weights, dims, inp, dout, din=None, stream=None):
     """dL/dW (numpy float32, NET_WEIGHTS) and, if din is given, dL/d(inp) into din."""
-    w, wp = _f32ptr(weights)
+    w, wp = _weights(weights)
+    _net_rows(dims, inp, dout, din)
     d = (C.c_int * 4)(*[int(x) for x in dims])
     dw = np.zeros(NET_WEIGHTS, dtype=np.float32)
     _check(None, lib().eofa_net_backward(wp, d, int(inp.shape[0]), _f32dev(inp), _f32dev(dout),
@@ -372,7 +391,7 @@ def eofa_train_preconditioner(ctx, sources, init_weights, opts, stream=None):
     """Train on the context's lattice; returns (weights numpy float32, stats)."""
     n = len(sources)
     sa = (C.c_void_p * n)(*[_dptr(t).value for t in sources])
-    w, wp = _f32ptr(init_weights)
+    w, wp = _weights(init_weights)
     out = np.zeros(NET_WEIGHTS, dtype=np.float32)
     st = eofa_train_stats()
     _check(ctx, lib().eofa_train_preconditioner(ctx, sa, n, wp, C.byref(opts), out.ctypes.data_as(_fp),
@@ -381,7 +400,7 @@ def eofa_train_preconditioner(ctx, sources, init_weights, opts, stream=None):
 
 
 def eofa_set_preconditioner(ctx, weights):
-    w, wp = _f32ptr(weights)
+    w, wp = _weights(weights)
     _check(ctx, lib().eofa_set_preconditioner(ctx, wp))
 
 
@@ -527,6 +546,16 @@ class Solver:
         st = eofa_heatbath(self.ctx, m1, m2, approx.alpha0, approx.alpha, approx.beta, eta, phi,
                            make_opts(**opts), pole_tol, forecast, stream, check)
         return phi, st
+
+    def train_preconditioner(self, sources, init_weights, opts, stream=None):
+        """eofa_train_preconditioner on this context's lattice, with the
+        sources' sizes checked; returns (weights, stats)."""
+        for t in sources:
+            _need(t, self._n5, "training source")
+        return eofa_train_preconditioner(self.ctx, sources, init_weights, opts, stream)
+
+    def set_preconditioner(self, weights):
+        eofa_set_preconditioner(self.ctx, weights)
 
     def close(self):
         if self.ctx is not None:

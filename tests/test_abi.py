@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -145,3 +146,14 @@ def test_more_argument_errors_without_gpu(libeofa):
     assert libeofa.eofa_tile_time(None, 1, 0, 0) == -1.0
     assert libeofa.eofa_hop_bytes(None, 1, 0) == 0.0
     libeofa.eofa_destroy(None)  # a no-op
+
+
+def test_binding_checks_network_weight_count():
+    """The library copies exactly NET_WEIGHTS weights from the host: the
+    binding refuses any other count before calling it."""
+    from paper_1706_05843_gb300 import binding as B
+    for call in (lambda w: B.eofa_net_forward(w, (4, 4, 4, 4), None, None),
+                 lambda w: B.eofa_net_backward(w, (4, 4, 4, 4), None, None),
+                 lambda w: B.eofa_set_preconditioner(None, w)):
+        with pytest.raises(ValueError):
+            call(np.zeros(B.NET_WEIGHTS - 1, dtype=np.float32))
