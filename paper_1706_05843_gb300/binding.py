@@ -327,6 +327,10 @@ def eofa_solve_batched(ctxs, rhss, sols, opts, stream=None, check=True):
 
 def eofa_apply_noalloc(params, gauge, inp, out, stream=None):
     """out = K inp without any device allocation (no context; small lattices)."""
+    V = int(np.prod([int(x) for x in params.dims]))
+    _need(gauge, V * 4 * 9, "gauge field")
+    _need(inp, V * int(params.Ls) * 12, "input field")
+    _need(out, V * int(params.Ls) * 12, "output field")
     _check(None, lib().eofa_apply_noalloc(C.byref(params), _dptr(gauge), _dptr(inp), _dptr(out),
                                           _stream(stream)))
 
