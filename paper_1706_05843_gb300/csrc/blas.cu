@@ -2,6 +2,8 @@
 // precision conversions, and the layout import/export kernels between the
 // caller's canonical complex128 fields and the internal even-odd blocked
 // layout.  One thread per 5D site (xcb, s) of a half lattice.
+#include <algorithm>
+
 #include "blas.h"
 #include "eofa.h"
 #include "learned.h"
@@ -11,6 +13,21 @@ namespace eofa {
 constexpr int BT = 256;  // threads per block of every kernel in this file
 
 static inline int grid_for(long n) { return (int)((n + BT - 1) / BT); }
+
+// grid of the grid-stride CG kernels: at most 4 blocks of BT threads per SM
+// (fewer partial sums for the last block to finalise)
+static int grid_capped(long n) {
+    static int cap = 0;
+    if (cap == 0) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            cap = 4 * sms;
+        else
+            cap = 1 << 30;
+    }
+    return std::max(1, std::min(grid_for(n), cap));
+}
 
 // ---------------------------------------------------------------------------
 // scalars
@@ -205,12 +222,11 @@ template <typename S>
 __global__ void __launch_bounds__(BT) k_cg_r(VecRef q, VecRef r, long n5, int Ls, Reduce rd, const int* done) {
     typedef typename Traits<S>::R R;
     if (*done) return;
-    const long t = (long)blockIdx.x * BT + threadIdx.x;
+    const R al = (R)rd.scal->alpha;
     R nn = (R)0;
-    if (t < n5) {
+    for (long t = (long)blockIdx.x * BT + threadIdx.x; t < n5; t += (long)gridDim.x * BT) {
         const long xcb = t / Ls;
         const int s = (int)(t - xcb * Ls);
-        const R al = (R)rd.scal->alpha;
         R qv[24], rv[24];
         load_sp<S, R>(q.d, q.n, xcb, s, Ls, qv);
         load_sp<S, R>(r.d, r.n, xcb, s, Ls, rv);
@@ -234,8 +250,7 @@ __global__ void __launch_bounds__(BT) k_cg_px(VecRef x, VecRef p, VecRef z, long
     typedef typename Traits<SX>::R RX;
     const DevScal* sc = rd.scal;
     if (sc->stop) return;
-    const long t = (long)blockIdx.x * BT + threadIdx.x;
-    if (t < n5) {
+    for (long t = (long)blockIdx.x * BT + threadIdx.x; t < n5; t += (long)gridDim.x * BT) {
         const long xcb = t / Ls;
         const int s = (int)(t - xcb * Ls);
         const double al = sc->alpha;
@@ -477,7 +492,7 @@ cudaError_t blas_cg_r(int prec, VecRef q, VecRef r, long n5, int Ls, Reduce rd, 
                       cudaStream_t st) {
     return dispatch_prec(prec, [&](auto* tag) -> cudaError_t {
         typedef std::remove_pointer_t<decltype(tag)> S;
-        k_cg_r<S><<<grid_for(n5), BT, 0, st>>>(q, r, n5, Ls, rd, done);
+        k_cg_r<S><<<grid_capped(n5), BT, 0, st>>>(q, r, n5, Ls, rd, done);
         return cudaGetLastError();
     });
 }
@@ -486,8 +501,8 @@ cudaError_t blas_cg_px(int prec, int xprec, VecRef x, VecRef p, VecRef z, long n
                        cudaStream_t st) {
     return dispatch_prec(prec, [&](auto* tag) -> cudaError_t {
         typedef std::remove_pointer_t<decltype(tag)> S;
-        if (xprec == 0) k_cg_px<S, double><<<grid_for(n5), BT, 0, st>>>(x, p, z, n5, Ls, rd);
-        else k_cg_px<S, float><<<grid_for(n5), BT, 0, st>>>(x, p, z, n5, Ls, rd);
+        if (xprec == 0) k_cg_px<S, double><<<grid_capped(n5), BT, 0, st>>>(x, p, z, n5, Ls, rd);
+        else k_cg_px<S, float><<<grid_capped(n5), BT, 0, st>>>(x, p, z, n5, Ls, rd);
         return cudaGetLastError();
     });
 }
