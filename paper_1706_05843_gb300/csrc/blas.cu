@@ -17,15 +17,13 @@ static inline int grid_for(long n) { return (int)((n + BT - 1) / BT); }
 // grid of the grid-stride CG kernels: at most 4 blocks of BT threads per SM
 // (fewer partial sums for the last block to finalise)
 static int grid_capped(long n) {
-    static int cap = 0;
-    if (cap == 0) {
+    static const int cap = [] {  // initialised once, thread-safe
         int dev = 0, sms = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
-            cap = 4 * sms;
-        else
-            cap = 1 << 30;
-    }
+            return 4 * sms;
+        return 1 << 30;
+    }();
     return std::max(1, std::min(grid_for(n), cap));
 }
 
