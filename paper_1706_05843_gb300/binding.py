@@ -353,8 +353,9 @@ def _net_rows(dims, *fields):
     """Every network field holds (slices, T, Z, Y, X, 24) float32 values."""
     n = int(fields[0].shape[0]) * int(np.prod([int(x) for x in dims])) * 24
     for f in fields:
-        if f is not None and f.numel() != n:
-            raise ValueError(f"network field: {f.numel()} values, the lattice and slice count need {n}")
+        size = None if f is None else (f.size if isinstance(f, np.ndarray) else f.numel())
+        if size is not None and size != n:
+            raise ValueError(f"network field: {size} values, the lattice and slice count need {n}")
 
 
 def _f32dev(t):

@@ -157,3 +157,16 @@ def test_binding_checks_network_weight_count():
                  lambda w: B.eofa_set_preconditioner(None, w)):
         with pytest.raises(ValueError):
             call(np.zeros(B.NET_WEIGHTS - 1, dtype=np.float32))
+
+
+def test_binding_size_checks_without_gpu():
+    """The Solver's size checks are host logic: a field of another size is
+    refused before any library call."""
+    from paper_1706_05843_gb300 import binding as B
+    B._need(np.zeros(24, dtype=np.complex128), 24, "field")
+    with pytest.raises(ValueError):
+        B._need(np.zeros(23, dtype=np.complex128), 24, "field")
+    with pytest.raises(ValueError):
+        B.solve_batched([object(), object()], [None], tol=1e-10)   # one rhs for two solvers
+    with pytest.raises(ValueError):
+        B._net_rows((2, 2, 2, 2), np.zeros((1, 2, 2, 2, 2, 23), dtype=np.float32))
